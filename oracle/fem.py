@@ -1,0 +1,182 @@
+"""Q1 finite-element pieces of the oracle (test infrastructure only).
+
+Follows §3.1 (global matrices M = [int rho C phi_m phi_n], K = [int k grad
+phi_m . grad phi_n], flux vector F) and §3.2 (element matrices M_e, K_e on a
+fixed grid, coefficients constant per element, assembly operator of Eq. 1).
+Element matrices are integrated with 2x2x2 Gauss quadrature, which is exact for
+trilinear shape functions on boxes.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+# local corner c of an element: (cx, cy, cz) = bits of c
+CORNERS = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], dtype=np.int64)
+_GP = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+
+
+def shape_q1(xi: float, eta: float, zeta: float):
+    """Trilinear shape functions on [-1,1]^3 and their reference gradients.
+
+    Returns N (8,) and dN (8, 3) for the corners in CORNERS order.
+    """
+    s = 2.0 * CORNERS - 1.0  # corner signs
+    fx = 1.0 + s[:, 0] * xi
+    fy = 1.0 + s[:, 1] * eta
+    fz = 1.0 + s[:, 2] * zeta
+    N = fx * fy * fz / 8.0
+    dN = np.stack([s[:, 0] * fy * fz, fx * s[:, 1] * fz, fx * fy * s[:, 2]], axis=1) / 8.0
+    return N, dN
+
+
+def element_matrices(hx: float, hy: float, hz: float):
+    """Element mass and stiffness matrices (8x8) of an hx*hy*hz box (§3.2).
+
+    M_e[a,b] = int N_a N_b dx,  K_e[a,b] = int grad N_a . grad N_b dx,
+    by 2x2x2 Gauss quadrature (x = x0 + (xi+1) h/2, so dx = (h/2) dxi).
+    """
+    detJ = hx * hy * hz / 8.0
+    inv_jac = np.array([2.0 / hx, 2.0 / hy, 2.0 / hz])
+    Me = np.zeros((8, 8))
+    Ke = np.zeros((8, 8))
+    for xi in _GP:
+        for eta in _GP:
+            for zeta in _GP:
+                N, dN = shape_q1(xi, eta, zeta)
+                G = dN * inv_jac  # physical gradients (8, 3)
+                Me += np.outer(N, N) * detJ
+                Ke += (G @ G.T) * detJ
+    return Me, Ke
+
+
+def spacing(nx, ny, nz, extent):
+    return extent[0] / nx, extent[1] / ny, extent[2] / nz
+
+
+def node_id(nx, ny, i, j, k):
+    return i + (nx + 1) * (j + (ny + 1) * k)
+
+
+def connectivity(nx: int, ny: int, nz: int) -> np.ndarray:
+    """(Ne, 8) global node ids of each element's corners, element order."""
+    ek, ej, ei = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ei, ej, ek = ei.ravel(), ej.ravel(), ek.ravel()
+    conn = np.empty((ei.size, 8), dtype=np.int64)
+    for c in range(8):
+        cx, cy, cz = CORNERS[c]
+        conn[:, c] = node_id(nx, ny, ei + cx, ej + cy, ek + cz)
+    return conn
+
+
+def assemble(nx, ny, nz, extent, coef: np.ndarray, which: str, chunk: int = 200_000):
+    """Global CSR matrix  sum_e coef_e * X_e  with X = M (mass) or K (stiffness).
+
+    This is the assembly operator of Eq. 1 carried out explicitly (the thing the
+    assembly-free method avoids), element by element in chunks.
+    """
+    Me, Ke = element_matrices(*spacing(nx, ny, nz, extent))
+    Xe = Me if which == "M" else Ke
+    n = (nx + 1) * (ny + 1) * (nz + 1)
+    conn = connectivity(nx, ny, nz)
+    coef = np.asarray(coef, dtype=np.float64)
+    total = None
+    for s in range(0, conn.shape[0], chunk):
+        c = conn[s:s + chunk]
+        rows = np.repeat(c, 8, axis=1).ravel()
+        cols = np.tile(c, (1, 8)).ravel()
+        vals = (coef[s:s + chunk, None, None] * Xe[None, :, :]).ravel()
+        part = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+        total = part if total is None else total + part
+    total.sum_duplicates()
+    return total
+
+
+def face_nodes(nx, ny, nz, face: int) -> np.ndarray:
+    """Node ids on a face (0:x0 1:x1 2:y0 3:y1 4:z0 5:z1)."""
+    ids = np.arange((nx + 1) * (ny + 1) * (nz + 1)).reshape(nz + 1, ny + 1, nx + 1)
+    return {0: ids[:, :, 0], 1: ids[:, :, nx], 2: ids[:, 0, :], 3: ids[:, ny, :],
+            4: ids[0, :, :], 5: ids[nz, :, :]}[face].ravel()
+
+
+def face_load(nx, ny, nz, extent, face: int, q: float) -> np.ndarray:
+    """F_i = int_face q phi_i ds for a constant inward flux q on one face (§3.1).
+
+    Each face quad carries bilinear shape functions; 2x2 Gauss quadrature.
+    """
+    n = (nx + 1) * (ny + 1) * (nz + 1)
+    F = np.zeros(n)
+    hx, hy, hz = spacing(nx, ny, nz, extent)
+    axis = face // 2
+    side = face % 2
+    dims = [d for d in range(3) if d != axis]
+    counts = (nx, ny, nz)
+    h = (hx, hy, hz)
+    detJ = h[dims[0]] * h[dims[1]] / 4.0
+    # integral of each bilinear corner function over the reference quad
+    wq = np.zeros(4)
+    for a in _GP:
+        for b in _GP:
+            for c, (ca, cb) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+                wq[c] += (1 + (2 * ca - 1) * a) * (1 + (2 * cb - 1) * b) / 4.0 * detJ
+    fixed = 0 if side == 0 else counts[axis]
+    for p in range(counts[dims[0]]):
+        for r in range(counts[dims[1]]):
+            for c, (ca, cb) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+                idx = [0, 0, 0]
+                idx[axis] = fixed
+                idx[dims[0]] = p + ca
+                idx[dims[1]] = r + cb
+                F[node_id(nx, ny, *idx)] += q * wq[c]
+    return F
+
+
+def flux_vector(p) -> np.ndarray:
+    """Sum of the face loads of all Neumann flux faces of a Problem."""
+    F = np.zeros(p.n_nodes)
+    for face, q in p.flux.items():
+        F += face_load(p.nx, p.ny, p.nz, p.extent, int(face), float(q))
+    return F
+
+
+def dirichlet_nodes(p):
+    """(ids, values) of the Dirichlet nodes; the lowest face id wins on overlaps."""
+    val = {}
+    for face in sorted(p.dirichlet, reverse=True):
+        for i in face_nodes(p.nx, p.ny, p.nz, int(face)):
+            val[int(i)] = float(p.dirichlet[face])
+    ids = np.array(sorted(val), dtype=np.int64)
+    return ids, np.array([val[i] for i in ids], dtype=np.float64)
+
+
+def apply_rows(p, x: np.ndarray, rows, sa: float, sb: float, eliminate: bool = True):
+    """(sa*M + sb*K) x at the listed rows only, element by element (Eq. 1, DbD form).
+
+    With eliminate=True the Dirichlet rows return x_i and Dirichlet columns are
+    dropped, i.e. the operator of the eliminated system padded with identity.
+    Used to check full-size GPU applies at sampled rows.
+    """
+    nx, ny, nz = p.nx, p.ny, p.nz
+    Me, Ke = element_matrices(*spacing(nx, ny, nz, p.extent))
+    dir_ids = set(dirichlet_nodes(p)[0].tolist()) if eliminate else set()
+    out = np.zeros(len(rows))
+    for t, i in enumerate(rows):
+        i = int(i)
+        if i in dir_ids:
+            out[t] = x[i]
+            continue
+        iz, rem = divmod(i, (nx + 1) * (ny + 1))
+        iy, ix = divmod(rem, nx + 1)
+        acc = 0.0
+        for c in range(8):  # this node is corner c of element (ix-cx, iy-cy, iz-cz)
+            ex, ey, ez = ix - CORNERS[c, 0], iy - CORNERS[c, 1], iz - CORNERS[c, 2]
+            if not (0 <= ex < nx and 0 <= ey < ny and 0 <= ez < nz):
+                continue
+            e = ex + nx * (ey + ny * ez)
+            for b in range(8):
+                j = node_id(nx, ny, ex + CORNERS[b, 0], ey + CORNERS[b, 1], ez + CORNERS[b, 2])
+                if j in dir_ids:
+                    continue
+                acc += (sa * p.rho_c[e] * Me[c, b] + sb * p.k[e] * Ke[c, b]) * x[j]
+        out[t] = acc
+    return out

@@ -1,0 +1,189 @@
+/*
+ * heat.h -- C ABI of the GB300 assembly-free transient heat solver.
+ *
+ * The library solves the theta-scheme step system of transient heat flow
+ * (§3.1), divided by dt:
+ *
+ *     [M/dt + theta K] U^n = [M/dt - (1 - theta) K] U^{n-1} + F^n,
+ *
+ * on a structured mesh of nx*ny*nz congruent trilinear (Q1) box elements with
+ * per-element coefficients rho*C and k (§3.2, "fixed grid"). M and K are never
+ * assembled: every product with A = M/dt + theta K is computed element by
+ * element from the closed-form Q1 element matrices (the assembly operator of
+ * §3.2 Eq. 1, read degree-of-freedom by degree-of-freedom). Each step is solved
+ * by Jacobi-preconditioned conjugate gradients (Algorithm 1, §3.3), entirely on
+ * one GPU.
+ *
+ * Conventions (all entry points):
+ *   - element (i,j,k), id = i + nx*(j + ny*k); node (i,j,k), id = i + (nx+1)*(j +
+ *     (ny+1)*k): x fastest (§4.1). N = (nx+1)(ny+1)(nz+1) nodes, Ne = nx*ny*nz.
+ *   - faces: 0 x=x0, 1 x=x1, 2 y=y0, 3 y=y1, 4 z=z0, 5 z=z1.
+ *   - Dirichlet faces are an extension (the paper has flux faces only): their
+ *     rows and columns are eliminated symmetrically; a node on several Dirichlet
+ *     faces takes the value of the lowest face id.
+ *   - "on_device" arguments: 0 = the pointer is host memory, 1 = device memory of
+ *     the current CUDA device. Device pointers are read/written on the sim's
+ *     stream; host pointers are copied synchronously.
+ *   - Every call returns heat_status. On error nothing is half-applied: the sim
+ *     keeps its previous state. heat_last_error() gives a thread-local message.
+ *   - Ownership: the library owns every device buffer it allocates; input arrays
+ *     are copied and stay the caller's; outputs go into caller buffers.
+ *   - Threading: one sim per thread (and per stream); the server is locked
+ *     internally.
+ */
+#ifndef HEAT_H
+#define HEAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct heat_mesh heat_mesh;
+typedef struct heat_sim heat_sim;
+typedef struct heat_batch heat_batch;
+typedef struct heat_server heat_server;
+
+typedef enum {
+  HEAT_OK = 0,
+  HEAT_ERR_ARG = 1,           /* bad argument (null, size, range, mismatch) */
+  HEAT_ERR_NOMEM = 2,         /* device memory or HBM budget exhausted */
+  HEAT_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  HEAT_ERR_NOT_CONVERGED = 4, /* max_iter reached; last iterate kept */
+  HEAT_ERR_NONFINITE = 5,     /* NaN/Inf in inputs or in a CG scalar */
+  HEAT_ERR_TIMEOUT = 6,       /* a bounded wait gave up */
+  HEAT_ERR_BUSY = 7,          /* no free slot / ticket not finished */
+  HEAT_ERR_BREAKDOWN = 8      /* CG breakdown: d^T A d <= 0 */
+} heat_status;
+
+typedef enum {
+  HEAT_FP64 = 0,         /* operator, vectors and dots in FP64 */
+  HEAT_FP32_REFINED = 1, /* FP32 operator/vectors, FP64 dots, FP64 outer refinement */
+  HEAT_FP32_PLAIN = 2    /* FP32 operator/vectors, FP64 dots, no refinement */
+} heat_precision;
+
+/* Solver parameters. heat_params_default() fills the defaults in brackets. */
+typedef struct {
+  double theta;      /* theta of the theta-scheme, 0 < theta <= 1   [0.5] (§3.1) */
+  double dt;         /* time step, > 0                              [1e-3] */
+  double rtol;       /* stop when r^T P^-1 r <= rtol^2 b^T P^-1 b   [1e-10] */
+  int max_iter;      /* CG iterations per step (all kinds), >= 1     [20000] */
+  int resid_period;  /* true residual r = b - A x every this many
+                        iterations (Algorithm 1 uses 50), >= 1       [50] */
+  int poll_period;   /* CG iterations queued between host polls      [32] */
+  int precision;     /* heat_precision                               [HEAT_FP64] */
+  double inner_rtol; /* FP32_REFINED: inner solve tolerance relative
+                        to its own right-hand side                   [1e-4] */
+  int max_outer;     /* FP32_REFINED: refinement sweeps per step     [40] */
+} heat_params;
+
+/* Boundary conditions (§3.1 strong form: k dT/dn = f on the sides). */
+typedef struct {
+  uint32_t dirichlet_faces;  /* bit f set: face f has fixed temperature */
+  double dirichlet_value[6]; /* value on each Dirichlet face */
+  double flux[6];            /* inward heat flux f on each face (ignored on
+                                Dirichlet faces); enters F (§3.1) */
+  int flux_steps;            /* F^n = F for steps n <= flux_steps, 0 after;
+                                < 0: on for every step */
+} heat_bc;
+
+/* Per-call statistics. */
+typedef struct {
+  int steps;                /* time steps completed by the call */
+  int status;               /* heat_status of the last step */
+  long long iters;          /* CG iterations (inner + outer) over the call */
+  long long outer;          /* refinement sweeps over the call (FP32_REFINED) */
+  int max_iters_step;       /* most CG iterations in one step */
+  double last_rel_residual; /* sqrt(r^T P^-1 r / b^T P^-1 b) at the last exit */
+  long long kernel_launches; /* kernels of this library launched by the call */
+} heat_step_stats;
+
+void heat_params_default(heat_params* p);
+
+/* Structured mesh on [origin, origin + extent] split into nx*ny*nz boxes
+ * (§4.1: domain divisions per dimension). nx, ny, nz >= 1, extent > 0. */
+heat_status heat_create_mesh(int nx, int ny, int nz, const double origin[3],
+                             const double extent[3], heat_mesh** out);
+void heat_destroy_mesh(heat_mesh* mesh);
+/* N and Ne of a mesh (either pointer may be NULL). */
+heat_status heat_mesh_sizes(const heat_mesh* mesh, long long* n_nodes, long long* n_elems);
+
+/* A simulation on `mesh` (kept by reference: the mesh must outlive the sim).
+ * cuda_stream: a cudaStream_t, or NULL for the legacy default stream. The sim
+ * starts with rho_c = k = 1 and U^0 = 0 (Dirichlet nodes at their values). */
+heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
+                            const heat_params* params, void* cuda_stream,
+                            heat_sim** out);
+void heat_destroy_sim(heat_sim* sim);
+
+/* Per-element coefficients rho*C (> 0) and k (> 0), Ne values each, element
+ * order (§3.2: constant per element). Rebuilds the Jacobi diagonal and the
+ * Dirichlet lift. HEAT_ERR_NONFINITE/ARG on NaN/Inf or non-positive values
+ * (checked for host input; device input is checked on the device). */
+heat_status heat_set_coeffs(heat_sim* sim, const double* rho_c, const double* k,
+                            int on_device);
+
+/* Change dt / theta / tolerances / precision between steps. */
+heat_status heat_set_params(heat_sim* sim, const heat_params* params);
+
+/* Set the current temperature U (N values, node order) and restart the time
+ * history (the next step extrapolates from U alone). Dirichlet nodes are
+ * overwritten with their face values. */
+heat_status heat_set_state(heat_sim* sim, const double* u, int on_device);
+/* Copy the current temperature U^n (N values) out. */
+heat_status heat_get_state(heat_sim* sim, double* u, int on_device);
+
+/* Advance nsteps time steps (Algorithm 1 per step, x0 = 2U^{n-1} - U^{n-2}).
+ * stats may be NULL. Returns the first failing step's status, if any. */
+heat_status heat_step(heat_sim* sim, int nsteps, heat_step_stats* stats);
+/* heat_step, then copy U^n to host u_out (may be NULL). */
+heat_status heat_solve_transient(heat_sim* sim, int nsteps, double* u_out,
+                                 heat_step_stats* stats);
+/* Number of completed steps, and the CG iterations of step s (0-based, of the
+ * last heat_step call); iters may be NULL. */
+heat_status heat_step_iterations(heat_sim* sim, int s, int* iters);
+
+/* ---- operator-level entry points (device pointers, sim stream) ---------- */
+
+/* y = A' x with A = M/dt + theta K (§3.2: A = M + theta dt K scaled by 1/dt),
+ * A' = A with Dirichlet rows and columns replaced by the identity. FP64. */
+heat_status heat_apply(heat_sim* sim, const double* x, double* y);
+/* Same operator in FP32 (the refined path's inner operator). */
+heat_status heat_apply_f32(heat_sim* sim, const float* x, float* y);
+/* General element-wise product y = sum_e A_e^T (sa*rho_c_e*Mhat + sb*k_e*Khat) A_e x
+ * without Dirichlet elimination (§3.2 Eq. 1), FP64: (sa, sb) = (1/dt, theta)
+ * gives A, (1/dt, theta-1) gives L, (1, 0) gives M, (0, 1) gives K. */
+heat_status heat_apply_general(heat_sim* sim, double sa, double sb, const double* x,
+                               double* y);
+/* Jacobi diagonal P = diag(A') (§3.3; P = 1 on Dirichlet rows), FP64, N values. */
+heat_status heat_diagonal(heat_sim* sim, double* p);
+/* Right-hand side of step n (1-based) from U^{n-1} = u_prev (§3.1):
+ * b = L u_prev + F^n - A_{.D} g on free rows, b = g on Dirichlet rows. FP64. */
+heat_status heat_rhs(heat_sim* sim, int n, const double* u_prev, double* b);
+/* Face flux vector F (flux on), FP64, N values. */
+heat_status heat_flux_vector(heat_sim* sim, double* f);
+
+/* ---- measurement -------------------------------------------------------- */
+
+/* Time `reps` CG iterations of the sim's current precision (the two tile
+ * kernels of one iteration of Algorithm 1: apply+direction+dot, then
+ * update+dot) with CUDA events recorded on the sim's stream around each
+ * launch. If flush != NULL, flush_bytes of it are overwritten before every
+ * timed launch (to evict L2). Outputs the mean ms per launch of each kernel
+ * and their algorithmic DRAM bytes per launch (vectors and coefficients each
+ * touched once). Needs a prior heat_step on the sim; leaves its solver state
+ * undefined (call heat_set_state before stepping again). */
+heat_status heat_profile_iteration(heat_sim* sim, int reps, void* flush, size_t flush_bytes,
+                                   double* ms_apply, double* ms_update,
+                                   double* bytes_apply, double* bytes_update);
+
+const char* heat_last_error(void);
+const char* heat_status_string(heat_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEAT_H */

@@ -1,0 +1,352 @@
+"""ctypes binding of include/heat.h (argument marshalling only).
+
+Function names match the C ABI. Device arrays are torch CUDA tensors (their
+``data_ptr()`` is passed through); host arrays are numpy float64 arrays.
+Every non-OK status raises HeatError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libheatgb.so")
+
+HEAT_OK = 0
+HEAT_ERR_ARG = 1
+HEAT_ERR_NOMEM = 2
+HEAT_ERR_CUDA = 3
+HEAT_ERR_NOT_CONVERGED = 4
+HEAT_ERR_NONFINITE = 5
+HEAT_ERR_TIMEOUT = 6
+HEAT_ERR_BUSY = 7
+HEAT_ERR_BREAKDOWN = 8
+
+HEAT_FP64 = 0
+HEAT_FP32_REFINED = 1
+HEAT_FP32_PLAIN = 2
+PRECISIONS = {"fp64": HEAT_FP64, "fp32_refined": HEAT_FP32_REFINED, "fp32_plain": HEAT_FP32_PLAIN}
+
+
+class HeatError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"heat status {status}: {message}")
+        self.status = status
+
+
+class heat_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("dt", C.c_double), ("rtol", C.c_double),
+                ("max_iter", C.c_int), ("resid_period", C.c_int), ("poll_period", C.c_int),
+                ("precision", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int)]
+
+
+class heat_bc(C.Structure):
+    _fields_ = [("dirichlet_faces", C.c_uint32), ("dirichlet_value", C.c_double * 6),
+                ("flux", C.c_double * 6), ("flux_steps", C.c_int)]
+
+
+class heat_step_stats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("status", C.c_int), ("iters", C.c_longlong),
+                ("outer", C.c_longlong), ("max_iters_step", C.c_int),
+                ("last_rel_residual", C.c_double), ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes); heat_status functions return c_int
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_SIGS = [
+    ("heat_params_default", None, [C.POINTER(heat_params)]),
+    ("heat_create_mesh", C.c_int, [C.c_int, C.c_int, C.c_int, _DP, _DP, C.POINTER(_VP)]),
+    ("heat_destroy_mesh", None, [_VP]),
+    ("heat_mesh_sizes", C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    ("heat_sim_create", C.c_int, [_VP, C.POINTER(heat_bc), C.POINTER(heat_params), _VP, C.POINTER(_VP)]),
+    ("heat_destroy_sim", None, [_VP]),
+    ("heat_set_coeffs", C.c_int, [_VP, _VP, _VP, C.c_int]),
+    ("heat_set_params", C.c_int, [_VP, C.POINTER(heat_params)]),
+    ("heat_set_state", C.c_int, [_VP, _VP, C.c_int]),
+    ("heat_get_state", C.c_int, [_VP, _VP, C.c_int]),
+    ("heat_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
+    ("heat_solve_transient", C.c_int, [_VP, C.c_int, _VP, C.POINTER(heat_step_stats)]),
+    ("heat_step_iterations", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
+    ("heat_apply", C.c_int, [_VP, _VP, _VP]),
+    ("heat_apply_f32", C.c_int, [_VP, _VP, _VP]),
+    ("heat_apply_general", C.c_int, [_VP, C.c_double, C.c_double, _VP, _VP]),
+    ("heat_diagonal", C.c_int, [_VP, _VP]),
+    ("heat_rhs", C.c_int, [_VP, C.c_int, _VP, _VP]),
+    ("heat_flux_vector", C.c_int, [_VP, _VP]),
+    ("heat_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
+    ("heat_last_error", C.c_char_p, []),
+    ("heat_status_string", C.c_char_p, [C.c_int]),
+]
+
+EXPORTED = [name for name, _, _ in _SIGS]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libheatgb.so (raises if it has not been built: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1905_07622_gb300.build.build() "
+                          "(the solver has no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != HEAT_OK:
+        raise HeatError(st, _lib.heat_last_error().decode())
+
+
+def _dev_ptr(t) -> int:
+    """Device pointer of a contiguous torch CUDA tensor."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _host_f64(a, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _arg(a, n):
+    """(pointer, on_device, keepalive) for a numpy host array or a CUDA tensor."""
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        if a.numel() != n:
+            raise ValueError(f"expected {n} values, got {a.numel()}")
+        return _dev_ptr(a), 1, a
+    h = _host_f64(a, n)
+    return h.ctypes.data, 0, h
+
+
+# ------------------------------------------------------------------ meshes
+
+def heat_params_default(**overrides) -> heat_params:
+    load_library()
+    p = heat_params()
+    _lib.heat_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(p, k, v)
+    return p
+
+
+def heat_create_mesh(nx, ny, nz, origin=(0.0, 0.0, 0.0), extent=(1.0, 1.0, 1.0)):
+    load_library()
+    o = (C.c_double * 3)(*origin)
+    e = (C.c_double * 3)(*extent)
+    out = C.c_void_p()
+    _check(_lib.heat_create_mesh(int(nx), int(ny), int(nz), o, e, C.byref(out)))
+    return out
+
+
+def heat_destroy_mesh(mesh):
+    if mesh:
+        _lib.heat_destroy_mesh(mesh)
+
+
+def heat_mesh_sizes(mesh):
+    nn, ne = C.c_longlong(), C.c_longlong()
+    _check(_lib.heat_mesh_sizes(mesh, C.byref(nn), C.byref(ne)))
+    return nn.value, ne.value
+
+
+def make_bc(dirichlet=None, flux=None, flux_steps=-1) -> heat_bc:
+    bc = heat_bc()
+    for f, v in (dirichlet or {}).items():
+        bc.dirichlet_faces |= 1 << int(f)
+        bc.dirichlet_value[int(f)] = float(v)
+    for f, q in (flux or {}).items():
+        bc.flux[int(f)] = float(q)
+    bc.flux_steps = int(flux_steps)
+    return bc
+
+
+def heat_sim_create(mesh, bc: heat_bc, params: heat_params, stream=None):
+    load_library()
+    out = C.c_void_p()
+    s = C.c_void_p(int(stream) if stream else 0)
+    _check(_lib.heat_sim_create(mesh, C.byref(bc), C.byref(params), s, C.byref(out)))
+    return out
+
+
+def heat_destroy_sim(sim):
+    if sim:
+        _lib.heat_destroy_sim(sim)
+
+
+def heat_set_coeffs(sim, rho_c, k, n_elems):
+    pr, dr, keep1 = _arg(rho_c, n_elems)
+    pk, dk, keep2 = _arg(k, n_elems)
+    if dr != dk:
+        raise ValueError("rho_c and k must both be host arrays or both CUDA tensors")
+    _check(_lib.heat_set_coeffs(sim, C.c_void_p(pr), C.c_void_p(pk), dr))
+
+
+def heat_set_params(sim, params: heat_params):
+    _check(_lib.heat_set_params(sim, C.byref(params)))
+
+
+def heat_set_state(sim, u, n_nodes):
+    p, dev, keep = _arg(u, n_nodes)
+    _check(_lib.heat_set_state(sim, C.c_void_p(p), dev))
+
+
+def heat_get_state(sim, n_nodes, out=None):
+    if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+        _check(_lib.heat_get_state(sim, C.c_void_p(_dev_ptr(out)), 1))
+        return out
+    u = np.empty(n_nodes, dtype=np.float64)
+    _check(_lib.heat_get_state(sim, C.c_void_p(u.ctypes.data), 0))
+    return u
+
+
+def heat_step(sim, nsteps: int) -> dict:
+    st = heat_step_stats()
+    _check(_lib.heat_step(sim, int(nsteps), C.byref(st)))
+    return st.as_dict()
+
+
+def heat_step_nocheck(sim, nsteps: int):
+    """heat_step returning (status, stats) instead of raising."""
+    st = heat_step_stats()
+    rc = _lib.heat_step(sim, int(nsteps), C.byref(st))
+    return rc, st.as_dict()
+
+
+def heat_solve_transient(sim, nsteps: int, n_nodes: int):
+    st = heat_step_stats()
+    u = np.empty(n_nodes, dtype=np.float64)
+    _check(_lib.heat_solve_transient(sim, int(nsteps), C.c_void_p(u.ctypes.data), C.byref(st)))
+    return u, st.as_dict()
+
+
+def heat_step_iterations(sim, step: int) -> int:
+    it = C.c_int()
+    _check(_lib.heat_step_iterations(sim, int(step), C.byref(it)))
+    return it.value
+
+
+def heat_apply(sim, x, y):
+    _check(_lib.heat_apply(sim, C.c_void_p(_dev_ptr(x)), C.c_void_p(_dev_ptr(y))))
+
+
+def heat_apply_f32(sim, x, y):
+    _check(_lib.heat_apply_f32(sim, C.c_void_p(_dev_ptr(x)), C.c_void_p(_dev_ptr(y))))
+
+
+def heat_apply_general(sim, sa, sb, x, y):
+    _check(_lib.heat_apply_general(sim, float(sa), float(sb), C.c_void_p(_dev_ptr(x)), C.c_void_p(_dev_ptr(y))))
+
+
+def heat_diagonal(sim, p):
+    _check(_lib.heat_diagonal(sim, C.c_void_p(_dev_ptr(p))))
+
+
+def heat_rhs(sim, n, u_prev, b):
+    _check(_lib.heat_rhs(sim, int(n), C.c_void_p(_dev_ptr(u_prev)), C.c_void_p(_dev_ptr(b))))
+
+
+def heat_flux_vector(sim, f):
+    _check(_lib.heat_flux_vector(sim, C.c_void_p(_dev_ptr(f))))
+
+
+def heat_profile_iteration(sim, reps: int, flush=None):
+    """Mean ms per launch and algorithmic bytes of the two CG-iteration kernels."""
+    ma, mu, ba, bu = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    fp = C.c_void_p(_dev_ptr(flush)) if flush is not None else C.c_void_p(0)
+    fb = flush.numel() * flush.element_size() if flush is not None else 0
+    _check(_lib.heat_profile_iteration(sim, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba), C.byref(bu)))
+    return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_last_error() -> str:
+    load_library()
+    return _lib.heat_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+@dataclass
+class Simulation:
+    """Owns a mesh + sim pair built from a workloads.Problem-like object."""
+
+    mesh: C.c_void_p
+    sim: C.c_void_p
+    n_nodes: int
+    n_elems: int
+
+    @classmethod
+    def from_problem(cls, p, precision="fp64", stream=None, coeffs_on_device=False, **param_overrides):
+        mesh = heat_create_mesh(p.nx, p.ny, p.nz, p.origin, p.extent)
+        try:
+            nn, ne = heat_mesh_sizes(mesh)
+            kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision)
+            kw.update(param_overrides)
+            prm = heat_params_default(**kw)
+            bc = make_bc(p.dirichlet, p.flux, p.flux_steps)
+            sim = heat_sim_create(mesh, bc, prm, stream)
+        except Exception:
+            heat_destroy_mesh(mesh)
+            raise
+        self = cls(mesh, sim, nn, ne)
+        try:
+            if coeffs_on_device:
+                import torch
+                rc = torch.as_tensor(p.rho_c, dtype=torch.float64, device="cuda")
+                kk = torch.as_tensor(p.k, dtype=torch.float64, device="cuda")
+                heat_set_coeffs(sim, rc, kk, ne)
+            else:
+                heat_set_coeffs(sim, p.rho_c, p.k, ne)
+            heat_set_state(sim, p.u0, nn)
+        except Exception:
+            self.close()
+            raise
+        return self
+
+    def step(self, nsteps):
+        return heat_step(self.sim, nsteps)
+
+    def state(self):
+        return heat_get_state(self.sim, self.n_nodes)
+
+    def set_params(self, **kw):
+        heat_set_params(self.sim, heat_params_default(**kw))
+
+    def close(self):
+        if self.sim:
+            heat_destroy_sim(self.sim)
+            self.sim = None
+        if self.mesh:
+            heat_destroy_mesh(self.mesh)
+            self.mesh = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+load_library()

@@ -1,0 +1,345 @@
+// The tick engine: a set of simulations advanced together by one captured
+// CUDA graph of phase-gated kernels. One tick is
+//   k_open, then iters_per_tick x (k_apply_dot, k_update),
+// over a device-side work list of (simulation, tile) pairs. Each simulation
+// carries its own phase, so simulations of different sizes, at different
+// steps and iterations, share every launch; the host only replays the graph
+// and polls a counter of unfinished simulations every few ticks (the paper's
+// host reads the residual after every iteration, §3.4.3).
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
+#include "engine.h"
+#include "tile_kernels.cuh"
+
+namespace heat {
+
+using TileFn = void (*)(const SimDev*, const int2*, const int*);
+
+struct KernelSet {
+  TileFn open, apply, update;
+  int tx, ty, tz;
+};
+
+template <int P, int TX, int TY, int TZ>
+static KernelSet make_set() {
+  using T = typename std::conditional<P == P_FP64, double, float>::type;
+  return {k_open<P, TX, TY, TZ>, k_apply_dot<T, TX, TY, TZ>, k_update<T, P, TX, TY, TZ>, TX, TY, TZ};
+}
+
+static KernelSet kernel_set(int prec) {
+  switch (prec) {
+    case P_FP64: return make_set<P_FP64, 32, 4, 8>();
+    case P_FP32_REFINED: return make_set<P_FP32_REFINED, 32, 4, 8>();
+    default: return make_set<P_FP32_PLAIN, 32, 4, 8>();
+  }
+}
+
+// Number of simulations not yet DONE or FAILED.
+__global__ void k_count_unfinished(const SimDev* __restrict__ sims, int nsims, int* out) {
+  int c = 0;
+  for (int i = threadIdx.x; i < nsims; i += blockDim.x) {
+    const int ph = *(volatile const int*)&sims[i].sc->phase;
+    c += (ph != PH_DONE && ph != PH_FAILED && ph != PH_IDLE) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  __shared__ int red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+struct Engine {
+  std::vector<heat_sim*> sims;
+  int prec = 0;
+  KernelSet ks{};
+  cudaStream_t stream = nullptr;
+  SimDev* d_sims = nullptr;
+  int2* d_work = nullptr;
+  int* d_nwork = nullptr;
+  int* d_unfinished = nullptr;
+  int* h_unfinished = nullptr;
+  double* d_partial = nullptr;
+  int nwork = 0, grid = 0, iters_per_tick = 8;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long launches = 0;  // kernels launched by the last engine_step_all
+  std::vector<SimDev> h_sims;
+  std::vector<int2> h_work;
+};
+
+static heat_status engine_upload(Engine* e) {
+  e->h_sims.clear();
+  e->h_work.clear();
+  long long tile_base = 0;
+  for (size_t i = 0; i < e->sims.size(); ++i) {
+    SimDev d = e->sims[i]->dev;
+    d.ntx = (d.nx + 1 + e->ks.tx - 1) / e->ks.tx;
+    d.nty = (d.ny + 1 + e->ks.ty - 1) / e->ks.ty;
+    d.ntz = (d.nz + 1 + e->ks.tz - 1) / e->ks.tz;
+    d.ntiles = d.ntx * d.nty * d.ntz;
+    d.partial = e->d_partial + 4 * tile_base;
+    for (int t = 0; t < d.ntiles; ++t) e->h_work.push_back(make_int2((int)i, t));
+    tile_base += d.ntiles;
+    e->h_sims.push_back(d);
+  }
+  e->nwork = (int)e->h_work.size();
+  CUDA_TRY(cudaMemcpyAsync(e->d_sims, e->h_sims.data(), sizeof(SimDev) * e->h_sims.size(), cudaMemcpyHostToDevice,
+                           e->stream));
+  CUDA_TRY(cudaMemcpyAsync(e->d_work, e->h_work.data(), sizeof(int2) * e->h_work.size(), cudaMemcpyHostToDevice,
+                           e->stream));
+  CUDA_TRY(cudaMemcpyAsync(e->d_nwork, &e->nwork, sizeof(int), cudaMemcpyHostToDevice, e->stream));
+  CUDA_TRY(cudaStreamSynchronize(e->stream));
+  return HEAT_OK;
+}
+
+static long long total_tiles(const std::vector<heat_sim*>& sims, const KernelSet& ks) {
+  long long t = 0;
+  for (heat_sim* s : sims) {
+    const long long a = (s->dev.nx + 1 + ks.tx - 1) / ks.tx, b = (s->dev.ny + 1 + ks.ty - 1) / ks.ty,
+                    c = (s->dev.nz + 1 + ks.tz - 1) / ks.tz;
+    t += a * b * c;
+  }
+  return t;
+}
+
+static heat_status engine_capture(Engine* e) {
+  if (e->gexec) {
+    cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+  }
+  if (e->graph) {
+    cudaGraphDestroy(e->graph);
+    e->graph = nullptr;
+  }
+  const int block = e->ks.tx * e->ks.ty;
+  // Capture on a private stream (the legacy default stream cannot capture);
+  // the instantiated graph is then launched on the engine's stream.
+  cudaStream_t cap;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    e->ks.open<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
+    for (int it = 0; it < e->iters_per_tick; ++it) {
+      e->ks.apply<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
+      e->ks.update<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
+    }
+    err = cudaStreamEndCapture(cap, &e->graph);
+  }
+  cudaStreamDestroy(cap);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(HEAT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(err));
+  }
+  CUDA_TRY(cudaGraphInstantiate(&e->gexec, e->graph, 0));
+  return HEAT_OK;
+}
+
+heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out) {
+  *out = nullptr;
+  if (nsims < 1 || !sims) return set_error(HEAT_ERR_ARG, "engine: no simulations");
+  Engine* e = new Engine();
+  e->sims.assign(sims, sims + nsims);
+  e->prec = precision;
+  e->ks = kernel_set(precision);
+  e->stream = stream;
+  const long long tiles = total_tiles(e->sims, e->ks);
+  if (tiles > (1LL << 30)) {
+    delete e;
+    return set_error(HEAT_ERR_ARG, "engine: too many tiles");
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e->grid = (int)std::max(1LL, std::min(tiles, (long long)sms * 8));
+  heat_status st = HEAT_OK;
+  auto fail = [&](heat_status s) {
+    engine_destroy(e);
+    return s;
+  };
+  if (cudaMalloc(&e->d_sims, sizeof(SimDev) * nsims) != cudaSuccess ||
+      cudaMalloc(&e->d_work, sizeof(int2) * tiles) != cudaSuccess ||
+      cudaMalloc(&e->d_nwork, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_partial, sizeof(double) * 4 * tiles) != cudaSuccess ||
+      cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(set_error(HEAT_ERR_NOMEM, "engine: device allocation failed"));
+  }
+  // the per-sim counters used by the last-block reductions start at zero
+  for (heat_sim* s : e->sims) {
+    st = sim_read_scalars(s);
+    if (st != HEAT_OK) return fail(st);
+    s->h_sc->count = 0;
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) return fail(st);
+  }
+  st = engine_upload(e);
+  if (st != HEAT_OK) return fail(st);
+  st = engine_capture(e);
+  if (st != HEAT_OK) return fail(st);
+  *out = e;
+  return HEAT_OK;
+}
+
+void engine_destroy(Engine* e) {
+  if (!e) return;
+  cudaStreamSynchronize(e->stream);
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  cudaFree(e->d_sims);
+  cudaFree(e->d_work);
+  cudaFree(e->d_nwork);
+  cudaFree(e->d_unfinished);
+  cudaFree(e->d_partial);
+  if (e->h_unfinished) cudaFreeHost(e->h_unfinished);
+  delete e;
+}
+
+heat_status engine_refresh(Engine* e) { return engine_upload(e); }
+
+heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters) {
+  int max_iter = 1, max_outer = 1, poll = 32;
+  for (heat_sim* s : e->sims) {
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    heat_status st = sim_read_scalars(s);
+    if (st != HEAT_OK) return st;
+    SimScalars* sc = s->h_sc;
+    sc->target = sc->step + nsteps;
+    sc->phase = PH_OPEN;
+    sc->status = ST_OK;
+    sc->count = 0;
+    if (reset_counters) {
+      sc->iters_total = 0;
+      sc->outer_total = 0;
+      sc->steps_total = 0;
+      sc->max_iters_step = 0;
+    }
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) return st;
+    max_iter = std::max(max_iter, s->prm.max_iter);
+    max_outer = std::max(max_outer, s->prm.max_outer);
+    poll = std::min(poll, s->prm.poll_period);
+  }
+  const int ticks_per_poll = std::max(1, poll / e->iters_per_tick);
+  // Every tick advances each unfinished simulation by at least one CG
+  // iteration or one phase change, so this bound is never reached by a
+  // healthy solve; it turns a logic error into HEAT_ERR_TIMEOUT.
+  const long long max_ticks = (long long)nsteps * (max_iter + 2LL * max_outer + 4) + 64;
+  long long ticks = 0;
+  e->launches = 0;
+  for (;;) {
+    for (int t = 0; t < ticks_per_poll; ++t) CUDA_TRY(cudaGraphLaunch(e->gexec, e->stream));
+    ticks += ticks_per_poll;
+    e->launches += (long long)ticks_per_poll * (1 + 2 * e->iters_per_tick) + 1;
+    k_count_unfinished<<<1, 256, 0, e->stream>>>(e->d_sims, (int)e->sims.size(), e->d_unfinished);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(e->h_unfinished, e->d_unfinished, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (*e->h_unfinished == 0) break;
+    if (ticks > max_ticks) return set_error(HEAT_ERR_TIMEOUT, "engine: solve did not finish within %lld ticks", ticks);
+  }
+  heat_status first_bad = HEAT_OK;
+  for (size_t i = 0; i < e->sims.size(); ++i) {
+    heat_sim* s = e->sims[i];
+    CUDA_TRY(cudaMemcpyAsync(s->h_sc, s->d_sc, sizeof(SimScalars), cudaMemcpyDeviceToHost, e->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(e->stream));
+  for (size_t i = 0; i < e->sims.size(); ++i) {
+    const SimScalars* sc = e->sims[i]->h_sc;
+    if (stats) {
+      heat_step_stats& o = stats[i];
+      o.steps = (int)sc->steps_total;
+      o.status = sc->phase == PH_FAILED ? sc->status : HEAT_OK;
+      o.iters = sc->iters_total;
+      o.outer = sc->outer_total;
+      o.max_iters_step = sc->max_iters_step;
+      o.last_rel_residual = sc->rel_res;
+      o.kernel_launches = e->launches;
+    }
+    if (sc->phase == PH_FAILED && first_bad == HEAT_OK) {
+      first_bad = (heat_status)sc->status;
+      set_error(first_bad, "simulation %zu failed at step %d: %s", i, sc->step + 1,
+                heat_status_string((heat_status)sc->status));
+    }
+  }
+  return first_bad;
+}
+
+heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
+                           double* ms_update, double* bytes_apply, double* bytes_update) {
+  heat_sim* s = e->sims[0];
+  const int block = e->ks.tx * e->ks.ty;
+  const int chunk = 40;  // below the inner-solve cap and the true-residual period
+  cudaEvent_t ev[4 * chunk];
+  for (int i = 0; i < 4 * chunk; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
+  double ta = 0.0, tu = 0.0;
+  heat_status st = HEAT_OK;
+  for (int done = 0; done < reps && st == HEAT_OK;) {
+    const int c = std::min(reps - done, chunk);
+    st = sim_read_scalars(s);
+    if (st != HEAT_OK) break;
+    SimScalars* sc = s->h_sc;
+    sc->phase = PH_ITER;
+    sc->iter = 1;
+    sc->iter_step = 0;
+    sc->restart = 1;
+    sc->thresh = -1.0;
+    sc->thresh_in = -1.0;
+    sc->count = 0;
+    if (!(sc->delta > 0.0)) sc->delta = 1.0;
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) break;
+    for (int i = 0; i < c; ++i) {
+      if (flush) cudaMemsetAsync(flush, i & 0xff, flush_bytes, e->stream);
+      cudaEventRecord(ev[4 * i + 0], e->stream);
+      e->ks.apply<<<e->grid, block, 0, e->stream>>>(e->d_sims, e->d_work, e->d_nwork);
+      cudaEventRecord(ev[4 * i + 1], e->stream);
+      if (flush) cudaMemsetAsync(flush, (i + 1) & 0xff, flush_bytes, e->stream);
+      cudaEventRecord(ev[4 * i + 2], e->stream);
+      e->ks.update<<<e->grid, block, 0, e->stream>>>(e->d_sims, e->d_work, e->d_nwork);
+      cudaEventRecord(ev[4 * i + 3], e->stream);
+    }
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      st = set_error(HEAT_ERR_CUDA, "profile: launch failed");
+      break;
+    }
+    for (int i = 0; i < c; ++i) {
+      float a = 0.f, u = 0.f;
+      cudaEventElapsedTime(&a, ev[4 * i + 0], ev[4 * i + 1]);
+      cudaEventElapsedTime(&u, ev[4 * i + 2], ev[4 * i + 3]);
+      ta += a;
+      tu += u;
+    }
+    st = sim_read_scalars(s);
+    if (st == HEAT_OK && s->h_sc->phase != PH_ITER)
+      st = set_error(HEAT_ERR_BREAKDOWN, "profile: the iteration left PH_ITER (status %d)", s->h_sc->status);
+    done += c;
+  }
+  for (int i = 0; i < 4 * chunk; ++i) cudaEventDestroy(ev[i]);
+  if (st != HEAT_OK) return st;
+  *ms_apply = ta / reps;
+  *ms_update = tu / reps;
+  // algorithmic bytes: every vector and coefficient touched once per launch
+  double ba = 0.0, bu = 0.0;
+  for (heat_sim* x : e->sims) {
+    const double n = (double)x->nn, ne = (double)x->ne;
+    if (e->prec == P_FP64) {
+      ba += n * (3 * 8 + 2 * 8) + ne * 16;  // r, P^-1, d_old in; d, q out; (rho_c, k)
+      bu += n * (2 * 8 + 8 + 2 * 8 + 8 + 8);  // x in/out, d, r in/out, q, P^-1
+    } else {
+      ba += n * (3 * 4 + 2 * 4) + ne * 8;
+      bu += n * (2 * 4 + 4 + 2 * 4 + 4 + 4);
+    }
+  }
+  *bytes_apply = ba;
+  *bytes_update = bu;
+  return HEAT_OK;
+}
+
+}  // namespace heat

@@ -1,0 +1,66 @@
+// Internal host-side structures shared by the C ABI and the tick engine.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "heat.h"
+#include "heat_dev.cuh"
+
+struct heat_mesh {
+  int nx, ny, nz;
+  double origin[3], extent[3];
+};
+
+namespace heat {
+struct Engine;
+}
+
+struct heat_sim {
+  const heat_mesh* mesh = nullptr;
+  heat_bc bc{};
+  heat_params prm{};
+  cudaStream_t stream = nullptr;
+  long long nn = 0, ne = 0;
+  std::vector<void*> allocs;          // device buffers owned by the sim
+  heat::SimDev dev{};                 // descriptor (host copy)
+  heat::SimDev* d_dev = nullptr;      // descriptor (device copy, per-node kernels)
+  heat::SimScalars* d_sc = nullptr;   // device scalars
+  heat::SimScalars* h_sc = nullptr;   // pinned host mirror
+  double* d_q6 = nullptr;
+  unsigned int* d_bad = nullptr;
+  int iters_log_cap = 0;
+  heat::Engine* eng = nullptr;        // single-simulation engine (lazy)
+};
+
+namespace heat {
+
+heat_status set_error(heat_status st, const char* fmt, ...);
+heat_status sim_alloc(heat_sim* s, void** p, size_t bytes);
+heat_status sim_upload_desc(heat_sim* s);
+heat_status sim_read_scalars(heat_sim* s);
+heat_status sim_write_scalars(heat_sim* s);
+
+// A set of simulations driven together by one captured tick graph.
+heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out);
+void engine_destroy(Engine* e);
+// Re-read the sims' descriptors (after a buffer or parameter change).
+heat_status engine_refresh(Engine* e);
+// Advance every sim of the engine by nsteps steps; stats[i] per sim (may be
+// NULL). reset_counters clears the per-call counters first.
+heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters);
+// Time reps CG iterations of the engine's first simulation (see heat_profile_iteration).
+heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
+                           double* ms_update, double* bytes_apply, double* bytes_update);
+
+}  // namespace heat
+
+#define CUDA_TRY(call)                                                                               \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      cudaGetLastError();                                                                            \
+      return heat::set_error(HEAT_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+    }                                                                                                \
+  } while (0)

@@ -1,0 +1,196 @@
+// Device-side data of the solver: per-simulation descriptors and scalars,
+// Q1 element-matrix classes, node/boundary helpers and reductions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace heat {
+
+// Per-simulation phase of the device-driven step machine. Kernels of a tick
+// act only on simulations whose phase matches them, so one launch sequence
+// can carry many simulations at different points of their solves.
+enum Phase : int {
+  PH_IDLE = 0,    // nothing queued
+  PH_OPEN = 1,    // start of a step: right-hand side, x0, first residual
+  PH_ITER = 2,    // CG iterations (FP64, or FP32 inner solve)
+  PH_OUTER = 3,   // FP32 path: x64 += e, FP64 true residual, restart inner
+  PH_DONE = 4,    // target step reached
+  PH_FAILED = 5   // status holds the error
+};
+
+enum Prec : int { P_FP64 = 0, P_FP32_REFINED = 1, P_FP32_PLAIN = 2 };
+
+// Status codes shared with heat.h.
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_NONFINITE = 5, ST_BREAKDOWN = 8 };
+
+// Device-resident scalars of one simulation (also mirrored to pinned host
+// memory for polling). Written only by the last block of a kernel for that
+// simulation, read by every block of later kernels.
+struct SimScalars {
+  int phase;
+  int status;
+  int step;        // completed steps since the last set_state
+  int target;      // phase becomes DONE when step == target
+  int iter;        // CG iterations of the current (inner) solve
+  int iter_step;   // CG iterations of the current step (inner + outer)
+  int outer;       // refinement sweeps of the current step
+  int restart;     // next apply takes d = P^-1 r (no previous direction)
+  int have_prev;   // U^{n-2} holds a valid state
+  int iu1, iu2, ix, ixa;  // vec64 pool slots: U^{n-1}, U^{n-2}, x, spare
+  int id;          // current direction slot (0/1)
+  int max_iters_step;
+  unsigned int count;  // tiles finished in the running kernel
+  int pad_;
+  double delta;    // r^T P^-1 r of the current solve
+  double delta_b;  // b^T P^-1 b of the step
+  double thresh;   // rtol^2 * delta_b
+  double thresh_in;  // inner threshold (FP32 paths)
+  double alpha, beta, dq;
+  double delta_out;  // FP64 true-residual r^T P^-1 r (FP32 paths)
+  double rel_res;    // sqrt(delta / delta_b) at the last step close
+  long long iters_total;  // CG iterations since the counters were cleared
+  long long outer_total;
+  long long steps_total;
+};
+
+struct SimDev {
+  int nx, ny, nz;             // elements per dimension
+  int ntx, nty, ntz, ntiles;  // tiles of the tile kernels
+  long long nn;               // nodes
+  uint32_t dir_faces;         // Dirichlet face bits
+  int prec;                   // Prec
+  int max_iter, resid_period, max_outer, flux_steps;
+  double g[6];                // Dirichlet values
+  double inv_dt, theta, rtol, inner_rtol;
+  double mhat[8], khat[8];    // element mass/stiffness entry by corner XOR pattern
+  float mhat_f[8], khat_f[8];
+  const double2* coef;        // (rho_c, k) per element
+  const float2* coef32;
+  double* vec64[4];           // U^{n-1}, U^{n-2}, x and spare (slots in SimScalars)
+  double* b;
+  double* r;
+  double* q;
+  double* d[2];
+  double* pinv;
+  double* zlift;              // A_{.D} g on free rows (Dirichlet lift)
+  double* F;                  // face flux vector
+  float* r32;
+  float* q32;
+  float* e32;
+  float* d32[2];
+  float* pinv32;
+  double* partial;            // 2 per tile
+  int* iters_log;             // CG iterations of each step
+  int iters_log_len;
+  SimScalars* sc;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ long long node_index(const SimDev& s, int i, int j, int k) {
+  return (long long)i + (long long)(s.nx + 1) * ((long long)j + (long long)(s.ny + 1) * k);
+}
+
+__device__ __forceinline__ bool inside_nodes(const SimDev& s, int i, int j, int k) {
+  return i >= 0 && j >= 0 && k >= 0 && i <= s.nx && j <= s.ny && k <= s.nz;
+}
+
+// Dirichlet test from the node's position (face BCs need no mask array).
+__device__ __forceinline__ bool is_dirichlet(const SimDev& s, int i, int j, int k) {
+  const uint32_t f = s.dir_faces;
+  return ((f & 1u) && i == 0) || ((f & 2u) && i == s.nx) || ((f & 4u) && j == 0) ||
+         ((f & 8u) && j == s.ny) || ((f & 16u) && k == 0) || ((f & 32u) && k == s.nz);
+}
+
+// Value of a Dirichlet node: the lowest face id that contains it.
+__device__ __forceinline__ double dirichlet_value(const SimDev& s, int i, int j, int k) {
+  const uint32_t f = s.dir_faces;
+  if ((f & 1u) && i == 0) return s.g[0];
+  if ((f & 2u) && i == s.nx) return s.g[1];
+  if ((f & 4u) && j == 0) return s.g[2];
+  if ((f & 8u) && j == s.ny) return s.g[3];
+  if ((f & 16u) && k == 0) return s.g[4];
+  if ((f & 32u) && k == s.nz) return s.g[5];
+  return 0.0;
+}
+
+template <class T> struct Coef2;
+template <> struct Coef2<double> { using type = double2; };
+template <> struct Coef2<float> { using type = float2; };
+
+template <class T> __device__ __forceinline__ const typename Coef2<T>::type* coef_ptr(const SimDev& s);
+template <> __device__ __forceinline__ const double2* coef_ptr<double>(const SimDev& s) { return s.coef; }
+template <> __device__ __forceinline__ const float2* coef_ptr<float>(const SimDev& s) { return s.coef32; }
+
+template <class T> __device__ __forceinline__ T mhat(const SimDev& s, int p);
+template <> __device__ __forceinline__ double mhat<double>(const SimDev& s, int p) { return s.mhat[p]; }
+template <> __device__ __forceinline__ float mhat<float>(const SimDev& s, int p) { return s.mhat_f[p]; }
+template <class T> __device__ __forceinline__ T khat(const SimDev& s, int p);
+template <> __device__ __forceinline__ double khat<double>(const SimDev& s, int p) { return s.khat[p]; }
+template <> __device__ __forceinline__ float khat<float>(const SimDev& s, int p) { return s.khat_f[p]; }
+
+// Block-wide sum of NV doubles; result valid in thread 0. `red` holds
+// NV * 32 doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * 32 + warp] = v[a];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = lane < nwarps ? red[a * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[a] = t;
+    }
+  }
+}
+
+// Publish this tile's partial sums and report whether the calling block
+// finished the simulation's last tile of this kernel. Only thread 0's return
+// value is meaningful; the caller broadcasts it. The last block then sums the
+// partials in tile order, so the result does not depend on which blocks ran
+// which tiles or on what else shares the launch.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const SimDev& s, int tile, const double (&v)[NV]) {
+  bool last = false;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s.partial[2 * tile + a] = v[a];
+    __threadfence();
+    unsigned int done = atomicAdd(&s.sc->count, 1u);
+    last = (done == (unsigned int)(s.ntiles - 1));
+    if (last) __threadfence();
+  }
+  return last;
+}
+
+// Ordered sum of the published partials (called by the last block).
+template <int NV>
+__device__ __forceinline__ void gather_partials(const SimDev& s, double (&out)[NV], double* red) {
+  double v[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = 0.0;
+  // fixed assignment of tiles to threads and a fixed reduction tree
+  for (int t = threadIdx.x; t < s.ntiles; t += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] += __ldcg(&s.partial[2 * t + a]);
+  }
+  block_sum<NV>(v, red);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = v[a];
+}
+
+}  // namespace heat

@@ -1,0 +1,155 @@
+// Per-node kernels: setup (diagonal, flux vector, Dirichlet lift, FP32
+// coefficients) and the operator-level entry points (apply, right-hand side).
+// One thread per node, grid-stride; included by the C ABI translation unit only.
+#pragma once
+
+#include "op.cuh"
+
+namespace heat {
+
+// --------------------------------------------------- per-node (setup) kernels
+
+// Jacobi diagonal (§3.3): P_i = sum_{e contains i} (rho_c_e/dt * Mhat[0] + theta*k_e*Khat[0]),
+// P = 1 on Dirichlet rows. Writes 1/P in FP64 and FP32.
+__global__ void k_setup_diag(const SimDev* __restrict__ sp) {
+  const SimDev& s = *sp;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    double p = 1.0;
+    if (!is_dirichlet(s, i, j, k)) {
+      double sa = 0.0, sk = 0.0;
+      for (int c = 0; c < 8; ++c) {
+        const int ex = i - (c & 1), ey = j - ((c >> 1) & 1), ez = k - ((c >> 2) & 1);
+        if (ex < 0 || ey < 0 || ez < 0 || ex >= s.nx || ey >= s.ny || ez >= s.nz) continue;
+        const double2 cf = s.coef[ex + (long long)s.nx * (ey + (long long)s.ny * ez)];
+        sa += cf.x;
+        sk += cf.y;
+      }
+      p = s.inv_dt * s.mhat[0] * sa + s.theta * s.khat[0] * sk;
+    }
+    s.pinv[n] = 1.0 / p;
+    s.pinv32[n] = (float)(1.0 / p);
+  }
+}
+
+// Face flux vector F_i = int_face q phi_i ds: on a face of h_a*h_b quads each
+// node gets q*h_a*h_b/4 per adjacent quad (1, 2 or 4 of them).
+__global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __restrict__ q6,
+                             double hx, double hy, double hz) {
+  const SimDev& s = *sp;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    const int ni = (i > 0 && i < s.nx) ? 2 : 1;
+    const int nj = (j > 0 && j < s.ny) ? 2 : 1;
+    const int nk = (k > 0 && k < s.nz) ? 2 : 1;
+    double f = 0.0;
+    if (i == 0) f += q6[0] * hy * hz * 0.25 * nj * nk;
+    if (i == s.nx) f += q6[1] * hy * hz * 0.25 * nj * nk;
+    if (j == 0) f += q6[2] * hx * hz * 0.25 * ni * nk;
+    if (j == s.ny) f += q6[3] * hx * hz * 0.25 * ni * nk;
+    if (k == 0) f += q6[4] * hx * hy * 0.25 * ni * nj;
+    if (k == s.nz) f += q6[5] * hx * hy * 0.25 * ni * nj;
+    s.F[n] = is_dirichlet(s, i, j, k) ? 0.0 : f;
+  }
+}
+
+// Dirichlet lift z = A_{.D} g on free rows (0 on Dirichlet rows).
+__global__ void k_setup_lift(const SimDev* __restrict__ sp) {
+  const SimDev& s = *sp;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    double z = 0.0;
+    if (s.dir_faces && !is_dirichlet(s, i, j, k)) {
+      z = gather_apply<double>(s, s.inv_dt, s.theta, i, j, k, [&](int a, int b, int c) -> double {
+        return is_dirichlet(s, a, b, c) ? dirichlet_value(s, a, b, c) : 0.0;
+      });
+    }
+    s.zlift[n] = z;
+  }
+}
+
+// FP32 copy of the coefficients; counts non-finite or non-positive entries.
+__global__ void k_setup_coef32(const SimDev* __restrict__ sp, long long ne, unsigned int* bad) {
+  const SimDev& s = *sp;
+  unsigned int nbad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 c = s.coef[e];
+    if (!(isfinite(c.x) && isfinite(c.y) && c.x > 0.0 && c.y > 0.0)) ++nbad;
+    reinterpret_cast<float2*>(const_cast<float2*>(s.coef32))[e] = make_float2((float)c.x, (float)c.y);
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+// Counts entries of (rho_c, k) that are non-finite or not > 0.
+__global__ void k_check_coef_pair(const double* __restrict__ rc, const double* __restrict__ kk, long long ne,
+                                  unsigned int* bad) {
+  unsigned int nbad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+    if (!(isfinite(rc[e]) && isfinite(kk[e]) && rc[e] > 0.0 && kk[e] > 0.0)) ++nbad;
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void k_reciprocal(const double* __restrict__ a, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = 1.0 / a[i];
+}
+
+// y = (sa M + sb K) x; with MASK, Dirichlet rows give y = x and Dirichlet
+// columns are dropped (the eliminated operator padded with the identity).
+template <class T, bool MASK>
+__global__ void k_apply_nodes(const SimDev* __restrict__ sp, T sa, T sb, const T* __restrict__ x,
+                              T* __restrict__ y) {
+  const SimDev& s = *sp;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    if (MASK && is_dirichlet(s, i, j, k)) {
+      y[n] = x[n];
+      continue;
+    }
+    y[n] = gather_apply<T>(s, sa, sb, i, j, k, [&](int a, int b, int c) -> T {
+      if (MASK && is_dirichlet(s, a, b, c)) return T(0);
+      return x[node_index(s, a, b, c)];
+    });
+  }
+}
+
+// Right-hand side of step n from u_prev: b = L u_prev + F^n - z (free rows), g (Dirichlet).
+__global__ void k_rhs_nodes(const SimDev* __restrict__ sp, int n_step, const double* __restrict__ u,
+                            double* __restrict__ b) {
+  const SimDev& s = *sp;
+  const bool flux_on = s.flux_steps < 0 || n_step <= s.flux_steps;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    if (is_dirichlet(s, i, j, k)) {
+      b[n] = dirichlet_value(s, i, j, k);
+      continue;
+    }
+    const double lu = gather_apply<double>(s, s.inv_dt, s.theta - 1.0, i, j, k,
+                                           [&](int a, int bb, int c) -> double { return u[node_index(s, a, bb, c)]; });
+    b[n] = lu + (flux_on ? s.F[n] : 0.0) - s.zlift[n];
+  }
+}
+
+// Overwrite Dirichlet nodes of u with their values.
+__global__ void k_impose_dirichlet(const SimDev* __restrict__ sp, double* __restrict__ u) {
+  const SimDev& s = *sp;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(s, n, i, j, k);
+    if (is_dirichlet(s, i, j, k)) u[n] = dirichlet_value(s, i, j, k);
+  }
+}
+
+}  // namespace heat

@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every symbol include/heat.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**\s*(heat_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    b = __graft_entry__._build_module()
+    b.build()
+    return ctypes.CDLL(b.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["heat_create_mesh", "heat_sim_create", "heat_set_coeffs", "heat_step",
+                     "heat_solve_transient", "heat_apply", "heat_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_covers_the_header():
+    import paper_1905_07622_gb300.api as api
+
+    assert set(declared_functions()) <= set(api.EXPORTED)
+
+
+def test_host_side_argument_checks_without_gpu(lib):
+    import paper_1905_07622_gb300.api as api
+
+    with pytest.raises(api.HeatError) as e:
+        api.heat_create_mesh(0, 3, 3)
+    assert e.value.status == api.HEAT_ERR_ARG
+    with pytest.raises(api.HeatError):
+        api.heat_create_mesh(2, 2, 2, extent=(1.0, -1.0, 1.0))
+    m = api.heat_create_mesh(3, 4, 5)
+    assert api.heat_mesh_sizes(m) == (4 * 5 * 6, 60)
+    api.heat_destroy_mesh(m)
+    p = api.heat_params_default()
+    assert p.resid_period == 50 and p.theta == 0.5

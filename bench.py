@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: forward transient solves of the 100^3 inclusions workload.
+
+One bench step is one complete forward simulation, as in the paper's inverse
+problem where each sample is a full transient solve (§5.3): set the
+per-element coefficients and the initial temperature, then run the 300
+theta-scheme steps (Jacobi-PCG per step, Algorithm 1) on the 100^3 Q1 mesh
+(1,030,301 DOF) with 200 spherical inclusions, FP32 operator with FP64 dots
+and FP64 iterative refinement, rtol 1e-10.
+
+Metric: DOF x CG-iterations per second (inner + outer iterations), whole job.
+  value: inputs already resident in HBM (device-to-device coefficient/state
+         upload inside the timed region).
+  e2e:   the same through the public host API (pinned host coefficients and
+         initial state copied in, final field copied out, every step).
+Between timed steps a 256 MiB buffer is overwritten to flush L2.
+
+--impl reference times the CPU oracle (test infrastructure, plain FP64 CSR
+Jacobi-PCG) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs its own independent forward solves
+(replicas, weak scaling), no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*CG-iters/s"
+UNIT = "DOF*iter/s"
+WORKLOAD = "inclusions_cube_100: Q1 100^3 (1,030,301 DOF), 200 spherical inclusions k=10 rho_c=3, flux pulse z=1 for 50 steps, dt=1e-3, theta=0.5, 300 steps per forward solve, rtol 1e-10"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nsteps", type=int, default=300, help="time steps per forward solve")
+    ap.add_argument("--precision", default="fp32_refined", choices=["fp64", "fp32_refined", "fp32_plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison solve")
+    ap.add_argument("--profile-reps", type=int, default=120)
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- oracle leg
+
+def cpu_worker(nsteps_sample: int):
+    """Runs in a fresh 1-thread process: oracle PCG on the first time steps."""
+    import workloads as W
+    from oracle import transient
+
+    p = W.inclusions_cube()
+    S = transient.build_system(p)  # assembly: setup, not timed
+    t0 = time.perf_counter()
+    res = transient.run(p, solver="pcg", nsteps=nsteps_sample, system=S)
+    dt = time.perf_counter() - t0
+    it = sum(res.iters)
+    print(json.dumps({"seconds": dt, "iters": it, "dof": p.n_nodes, "steps": nsteps_sample,
+                      "value": p.n_nodes * it / dt}))
+
+
+def run_cpu_baseline(nsteps_sample: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(nsteps_sample)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu baseline failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel_key)
+    except Exception:
+        return None
+    if not d:
+        return None
+    h = hashlib.sha256()
+    for f in d.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != d.get("sha256"):
+        return None  # kernel changed since the counters were taken
+    return d.get("dram_bytes_per_launch")
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 CSR Jacobi-PCG, 1 host thread), each step one time step."""
+    if rank != 0:
+        return
+    import workloads as W
+    from oracle import transient
+
+    p = W.inclusions_cube()
+    S = transient.build_system(p)
+    u_prev, u_prev2 = p.u0.copy(), None
+    from oracle import pcg
+    times, iters = [], []
+    n = 0
+    for k in range(args.warmup + args.steps):
+        n += 1
+        t0 = time.perf_counter()
+        b = transient.step_rhs(p, S, u_prev, n)
+        x0 = u_prev if u_prev2 is None else 2 * u_prev - u_prev2
+        x, it, _, _ = pcg.pcg(S.A_ff, b, x0[S.free], S.pinv_f, p.rtol)
+        dt = time.perf_counter() - t0
+        u_new = x
+        u_prev2, u_prev = u_prev, u_new
+        if k >= args.warmup:
+            times.append(dt)
+            iters.append(it)
+    T = sum(times)
+    value = p.n_nodes * sum(iters) / T
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (host)",
+                                            "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1") or 1),
+                             "kind": "oracle",
+                             "sample": f"steps 1..{args.warmup + args.steps} of the 300-step transient, one per bench step; assembly untimed"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters": iters}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+        return
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        return
+
+    # the CPU baseline runs in a fresh process before this one touches the GPU
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(2)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1905_07622_gb300 as hg
+    import workloads as W
+
+    p = W.inclusions_cube(nsteps=args.nsteps)
+    stream = torch.cuda.current_stream()
+    sim = hg.Simulation.from_problem(p, precision=args.precision, stream=stream.cuda_stream)
+    nn, ne = sim.n_nodes, sim.n_elems
+    rc_d = torch.tensor(p.rho_c, device="cuda")
+    k_d = torch.tensor(p.k, device="cuda")
+    u0_d = torch.tensor(p.u0, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def forward_device():
+        hg.heat_set_coeffs(sim.sim, rc_d, k_d, ne)
+        hg.heat_set_state(sim.sim, u0_d, nn)
+        return hg.heat_step(sim.sim, args.nsteps)
+
+    # pinned host inputs/outputs for the end-to-end leg
+    rc_h = torch.tensor(p.rho_c).pin_memory().numpy()
+    k_h = torch.tensor(p.k).pin_memory().numpy()
+    u0_h = torch.tensor(p.u0).pin_memory().numpy()
+    u_out = torch.empty(nn, dtype=torch.float64).pin_memory().numpy()
+
+    def forward_host():
+        hg.heat_set_coeffs(sim.sim, rc_h, k_h, ne)
+        hg.heat_set_state(sim.sim, u0_h, nn)
+        return hg.heat_solve_transient_into(sim.sim, args.nsteps, u_out)
+
+    def timed(fn, K, W_):
+        for _ in range(W_):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        ms, its, launches = [], 0, 0
+        for _ in range(K):
+            flush.random_(0, 255)  # evict L2 between timed steps (not timed)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            its += st["iters"]
+            launches += st["kernel_launches"]
+        torch.cuda.synchronize()
+        barrier(world)
+        return ms, its, launches
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, its, launches = timed(forward_device, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_e2e, its_e2e, _ = timed(forward_host, args.steps, 1)
+
+    T = max_over_ranks(world, sum(ms) / 1e3)
+    units = sum_over_ranks(world, float(nn) * its)
+    value = units / T
+    T2 = max_over_ranks(world, sum(ms_e2e) / 1e3)
+    value_e2e = sum_over_ranks(world, float(nn) * its_e2e) / T2
+
+    # accuracy of this configuration's final field vs the FP64 path (same GPU)
+    u_ref = None
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        sim64 = hg.Simulation.from_problem(p, precision="fp64", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st64 = sim64.step(args.nsteps)
+        b.record(stream)
+        b.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        u_ref = sim64.state()
+        fp64 = {"value": nn * st64["iters"] / t64, "unit": UNIT, "iters": st64["iters"],
+                "ms_per_forward_solve": t64 * 1e3}
+        sim64.close()
+    final_err = None
+    if u_ref is not None:
+        u = sim.state()
+        final_err = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+
+    # dominant kernel (apply + direction + d.q of the inner solve), timed alone
+    # with CUDA events on this stream, L2 flushed before each launch
+    prof = hg.heat_profile_iteration(sim.sim, args.profile_reps, flush)
+    peak, peak_kind = measured_peaks()
+    achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
+    kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
+    traffic = ncu_traffic(kernel_key)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32_refined": "f32+f64", "fp32_plain": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "dof": nn,
+                       "time_steps_per_forward_solve": args.nsteps, "cg_iterations_per_step_avg": its / (args.steps * args.nsteps),
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "flushed between timed steps (256 MiB overwrite)"},
+            "e2e": {"value": value_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (2 * ne + nn), "d2h_bytes_per_step": 8 * nn},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": kernel_key.split("@")[0], "peak_kind": f"{peak_kind} HBM copy (burst)",
+                         "ms_per_launch": prof["ms_apply"], "algorithmic_bytes_per_launch": prof["bytes_apply"],
+                         "update_kernel": {"ms_per_launch": prof["ms_update"], "algorithmic_bytes_per_launch": prof["bytes_update"],
+                                           "achieved": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9}},
+            "clocks": clocks,
+            "fp64_path": fp64,
+            "final_field_rel_err_vs_fp64_path": final_err,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"oracle Jacobi-PCG, first {cpu['steps']} time steps of the same workload ({cpu['iters']} CG iterations, {cpu['seconds']:.1f} s; CSR assembly untimed)"}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -242,6 +242,15 @@ def heat_solve_transient(sim, nsteps: int, n_nodes: int):
     return u, st.as_dict()
 
 
+def heat_solve_transient_into(sim, nsteps: int, u_out: np.ndarray) -> dict:
+    """heat_solve_transient into a caller-owned (e.g. pinned) float64 host array."""
+    if u_out.dtype != np.float64 or not u_out.flags["C_CONTIGUOUS"]:
+        raise ValueError("u_out must be a contiguous float64 array")
+    st = heat_step_stats()
+    _check(_lib.heat_solve_transient(sim, int(nsteps), C.c_void_p(u_out.ctypes.data), C.byref(st)))
+    return st.as_dict()
+
+
 def heat_step_iterations(sim, step: int) -> int:
     it = C.c_int()
     _check(_lib.heat_step_iterations(sim, int(step), C.byref(it)))

@@ -165,6 +165,33 @@ heat_status heat_rhs(heat_sim* sim, int n, const double* u_prev, double* b);
 /* Face flux vector F (flux on), FP64, N values. */
 heat_status heat_flux_vector(heat_sim* sim, double* f);
 
+/* ---- allocation-free operator call ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running during CUDA graph capture
+ * (allocation cannot be captured), real-time loops that forbid allocation after
+ * start-up, and hosts whose memory manager owns all device memory. It computes
+ * y = A' x and *xdoty = x . A' x (A' as in heat_apply) on caller-owned device
+ * buffers and allocates nothing: its reduction scratch (one partial sum per
+ * tile of 32x4x8 nodes, and a counter) lives in a fixed 32 KiB device array
+ * that every GPU loading the library holds until exit.
+ *   nx, ny, nz, extent: the mesh, as in heat_create_mesh. At most
+ *     HEAT_NOALLOC_MAX_TILES tiles, i.e. ceil((nx+1)/32)*ceil((ny+1)/4)*
+ *     ceil((nz+1)/8) <= 4096 (for example 127^3 elements); larger meshes
+ *     return HEAT_ERR_ARG without launching anything.
+ *   dt, theta, dirichlet_faces: as in heat_params / heat_bc.
+ *   coef: device, 2*Ne doubles, (rho_c, k) interleaved per element, element
+ *     order, 16-byte aligned. x, y: device, N doubles. xdoty: device, 1 double.
+ *   cuda_stream: stream of the launch (NULL: legacy default stream).
+ * Calls share the scratch array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (other streams or host threads) race: the
+ * caller must serialise them. The first call on each device looks up the
+ * array's address with that device current; make it before any stream
+ * capture. The call is asynchronous on cuda_stream. */
+#define HEAT_NOALLOC_MAX_TILES 4096
+heat_status heat_apply_dot_noalloc(int nx, int ny, int nz, const double extent[3], double dt,
+                                   double theta, uint32_t dirichlet_faces, const double* coef,
+                                   const double* x, double* y, double* xdoty, void* cuda_stream);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Time `reps` CG iterations of the sim's current precision (the two tile

@@ -84,6 +84,8 @@ _SIGS = [
     ("heat_rhs", C.c_int, [_VP, C.c_int, _VP, _VP]),
     ("heat_flux_vector", C.c_int, [_VP, _VP]),
     ("heat_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
+    ("heat_apply_dot_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, _DP, C.c_double, C.c_double, C.c_uint32,
+                                         _VP, _VP, _VP, _VP, _VP]),
     ("heat_last_error", C.c_char_p, []),
     ("heat_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -288,6 +290,16 @@ def heat_profile_iteration(sim, reps: int, flush=None):
     fb = flush.numel() * flush.element_size() if flush is not None else 0
     _check(_lib.heat_profile_iteration(sim, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba), C.byref(bu)))
     return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_apply_dot_noalloc(nx, ny, nz, extent, dt, theta, dirichlet_faces, coef, x, y, xdoty, stream=None):
+    """Allocation-free y = A' x and x.A'x on caller-owned CUDA tensors (see include/heat.h)."""
+    load_library()
+    ext = (C.c_double * 3)(*extent)
+    s = C.c_void_p(int(stream) if stream else 0)
+    _check(_lib.heat_apply_dot_noalloc(int(nx), int(ny), int(nz), ext, float(dt), float(theta),
+                                       int(dirichlet_faces), C.c_void_p(_dev_ptr(coef)), C.c_void_p(_dev_ptr(x)),
+                                       C.c_void_p(_dev_ptr(y)), C.c_void_p(_dev_ptr(xdoty)), s))
 
 
 def heat_last_error() -> str:

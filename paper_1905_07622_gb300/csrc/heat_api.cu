@@ -97,7 +97,7 @@ extern "C" heat_status heat_mesh_sizes(const heat_mesh* m, long long* n_nodes, l
 // pattern p of two corners (bit d set: the corners differ in dimension d):
 // tensor products of the 1-D linear-element mass h/6*[2 1;1 2] and stiffness
 // 1/h*[1 -1;-1 1] (§3.2: one element matrix pair serves the whole fixed grid).
-static void element_classes(double hx, double hy, double hz, double mhat[8], double khat[8]) {
+void heat::element_classes(double hx, double hy, double hz, double mhat[8], double khat[8]) {
   const double h[3] = {hx, hy, hz};
   for (int p = 0; p < 8; ++p) {
     double m[3], kk[3];

@@ -1,11 +1,12 @@
 // The tick engine: a set of simulations advanced together by one captured
 // CUDA graph of phase-gated kernels. One tick is
 //   k_open, then iters_per_tick x (k_apply_dot, k_update),
-// over a device-side work list of (simulation, tile) pairs. Each simulation
-// carries its own phase, so simulations of different sizes, at different
-// steps and iterations, share every launch; the host only replays the graph
-// and polls a counter of unfinished simulations every few ticks (the paper's
-// host reads the residual after every iteration, §3.4.3).
+// over device-side work lists of (simulation, operator tile) and
+// (simulation, pointwise chunk) pairs. Each simulation carries its own phase,
+// so simulations of different sizes, at different steps and iterations, share
+// every launch; the host only replays the graph and polls a counter of
+// unfinished simulations every few ticks (the paper's host reads the residual
+// back after every iteration, §3.4.3).
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -19,20 +20,21 @@ using TileFn = void (*)(const SimDev*, const int2*, const int*);
 
 struct KernelSet {
   TileFn open, apply, update;
-  int tx, ty, tz;
+  int sx, sy;
+  int open_threads, apply_threads;
 };
 
-template <int P, int TX, int TY, int TZ>
+template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
-  return {k_open<P, TX, TY, TZ>, k_apply_dot<T, TX, TY, TZ>, k_update<T, P, TX, TY, TZ>, TX, TY, TZ};
+  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY};
 }
 
 static KernelSet kernel_set(int prec) {
   switch (prec) {
-    case P_FP64: return make_set<P_FP64, 32, 4, 8>();
-    case P_FP32_REFINED: return make_set<P_FP32_REFINED, 32, 4, 8>();
-    default: return make_set<P_FP32_PLAIN, 32, 4, 8>();
+    case P_FP64: return make_set<P_FP64, 16, 16>();
+    case P_FP32_REFINED: return make_set<P_FP32_REFINED, 16, 16>();
+    default: return make_set<P_FP32_PLAIN, 16, 16>();
   }
 }
 
@@ -60,52 +62,81 @@ struct Engine {
   KernelSet ks{};
   cudaStream_t stream = nullptr;
   SimDev* d_sims = nullptr;
-  int2* d_work = nullptr;
-  int* d_nwork = nullptr;
+  int2* d_work_op = nullptr;
+  int2* d_work_pw = nullptr;
+  int* d_nwork = nullptr;  // [0] operator items, [1] pointwise items
   int* d_unfinished = nullptr;
   int* h_unfinished = nullptr;
   double* d_partial = nullptr;
-  int nwork = 0, grid = 0, iters_per_tick = 8;
+  long long cap_op = 0, cap_pw = 0, cap_partial = 0;
+  int grid_op = 0, grid_pw = 0, iters_per_tick = 4;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long launches = 0;  // kernels launched by the last engine_step_all
   std::vector<SimDev> h_sims;
-  std::vector<int2> h_work;
+  std::vector<int2> h_op, h_pw;
 };
+
+// Operator tile geometry of one simulation: (SX-1) x (SY-1) node columns per
+// tile, tz_len levels. tz_len trades z-halo work (3 extra levels per tile)
+// against the number of tiles; aim for at least `want` tiles in total.
+static void tile_geometry(SimDev& d, const KernelSet& ks, long long want_tiles_this_sim) {
+  d.ntx = (d.nx + 1 + ks.sx - 2) / (ks.sx - 1);
+  d.nty = (d.ny + 1 + ks.sy - 2) / (ks.sy - 1);
+  const int levels = d.nz + 1;
+  const long long cols = (long long)d.ntx * d.nty;
+  int ntz = (int)std::max(1LL, std::min<long long>(levels, (want_tiles_this_sim + cols - 1) / cols));
+  // at least 8 levels per tile keeps the z-halo overhead below 40 %
+  ntz = std::min(ntz, std::max(1, levels / 8));
+  d.tz_len = (levels + ntz - 1) / ntz;
+  d.ntz = (levels + d.tz_len - 1) / d.tz_len;
+  d.ntiles = d.ntx * d.nty * d.ntz;
+  d.npw = (int)((d.nn + kPwChunk - 1) / kPwChunk);
+}
+
+static int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
 
 static heat_status engine_upload(Engine* e) {
   e->h_sims.clear();
-  e->h_work.clear();
-  long long tile_base = 0;
+  e->h_op.clear();
+  e->h_pw.clear();
+  const int sms = sm_count();
+  long long total_nodes = 0;
+  for (heat_sim* s : e->sims) total_nodes += s->nn;
+  long long item_base = 0;
   for (size_t i = 0; i < e->sims.size(); ++i) {
     SimDev d = e->sims[i]->dev;
-    d.ntx = (d.nx + 1 + e->ks.tx - 1) / e->ks.tx;
-    d.nty = (d.ny + 1 + e->ks.ty - 1) / e->ks.ty;
-    d.ntz = (d.nz + 1 + e->ks.tz - 1) / e->ks.tz;
-    d.ntiles = d.ntx * d.nty * d.ntz;
-    d.partial = e->d_partial + 4 * tile_base;
-    for (int t = 0; t < d.ntiles; ++t) e->h_work.push_back(make_int2((int)i, t));
-    tile_base += d.ntiles;
+    // share of ~3 waves of 2 resident tiles per SM, by node count
+    const long long want = std::max(1LL, (long long)(6.0 * sms * (double)d.nn / (double)total_nodes));
+    tile_geometry(d, e->ks, want);
+    d.partial = e->d_partial + 4 * item_base;
+    item_base += std::max(d.ntiles, d.npw);
+    for (int t = 0; t < d.ntiles; ++t) e->h_op.push_back(make_int2((int)i, t));
+    for (int t = 0; t < d.npw; ++t) e->h_pw.push_back(make_int2((int)i, t));
     e->h_sims.push_back(d);
   }
-  e->nwork = (int)e->h_work.size();
+  if ((long long)e->h_op.size() > e->cap_op || (long long)e->h_pw.size() > e->cap_pw || item_base > e->cap_partial)
+    return set_error(HEAT_ERR_ARG, "engine: work lists exceed their capacity");
+  const int nwork[2] = {(int)e->h_op.size(), (int)e->h_pw.size()};
   CUDA_TRY(cudaMemcpyAsync(e->d_sims, e->h_sims.data(), sizeof(SimDev) * e->h_sims.size(), cudaMemcpyHostToDevice,
                            e->stream));
-  CUDA_TRY(cudaMemcpyAsync(e->d_work, e->h_work.data(), sizeof(int2) * e->h_work.size(), cudaMemcpyHostToDevice,
+  CUDA_TRY(cudaMemcpyAsync(e->d_work_op, e->h_op.data(), sizeof(int2) * e->h_op.size(), cudaMemcpyHostToDevice,
                            e->stream));
-  CUDA_TRY(cudaMemcpyAsync(e->d_nwork, &e->nwork, sizeof(int), cudaMemcpyHostToDevice, e->stream));
+  CUDA_TRY(cudaMemcpyAsync(e->d_work_pw, e->h_pw.data(), sizeof(int2) * e->h_pw.size(), cudaMemcpyHostToDevice,
+                           e->stream));
+  CUDA_TRY(cudaMemcpyAsync(e->d_nwork, nwork, sizeof(nwork), cudaMemcpyHostToDevice, e->stream));
   CUDA_TRY(cudaStreamSynchronize(e->stream));
+  int occ_op = 1, occ_pw = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_op, e->ks.apply, e->ks.apply_threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pw, e->ks.update, kPwThreads, 0);
+  e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
+  e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
   return HEAT_OK;
-}
-
-static long long total_tiles(const std::vector<heat_sim*>& sims, const KernelSet& ks) {
-  long long t = 0;
-  for (heat_sim* s : sims) {
-    const long long a = (s->dev.nx + 1 + ks.tx - 1) / ks.tx, b = (s->dev.ny + 1 + ks.ty - 1) / ks.ty,
-                    c = (s->dev.nz + 1 + ks.tz - 1) / ks.tz;
-    t += a * b * c;
-  }
-  return t;
 }
 
 static heat_status engine_capture(Engine* e) {
@@ -117,17 +148,16 @@ static heat_status engine_capture(Engine* e) {
     cudaGraphDestroy(e->graph);
     e->graph = nullptr;
   }
-  const int block = e->ks.tx * e->ks.ty;
   // Capture on a private stream (the legacy default stream cannot capture);
   // the instantiated graph is then launched on the engine's stream.
   cudaStream_t cap;
   CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
-    e->ks.open<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
+    e->ks.open<<<e->grid_op, e->ks.open_threads, 0, cap>>>(e->d_sims, e->d_work_op, e->d_nwork);
     for (int it = 0; it < e->iters_per_tick; ++it) {
-      e->ks.apply<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
-      e->ks.update<<<e->grid, block, 0, cap>>>(e->d_sims, e->d_work, e->d_nwork);
+      e->ks.apply<<<e->grid_op, e->ks.apply_threads, 0, cap>>>(e->d_sims, e->d_work_op, e->d_nwork);
+      e->ks.update<<<e->grid_pw, kPwThreads, 0, cap>>>(e->d_sims, e->d_work_pw, e->d_nwork + 1);
     }
     err = cudaStreamEndCapture(cap, &e->graph);
   }
@@ -148,25 +178,35 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   e->prec = precision;
   e->ks = kernel_set(precision);
   e->stream = stream;
-  const long long tiles = total_tiles(e->sims, e->ks);
-  if (tiles > (1LL << 30)) {
-    delete e;
-    return set_error(HEAT_ERR_ARG, "engine: too many tiles");
+  // capacities: the largest tile count any geometry choice can give, and the chunks
+  long long cap_op = 0, cap_pw = 0, cap_partial = 0;
+  for (heat_sim* s : e->sims) {
+    const long long cols = (long long)((s->dev.nx + e->ks.sx - 1) / (e->ks.sx - 1)) *
+                           ((s->dev.ny + e->ks.sy - 1) / (e->ks.sy - 1));
+    const long long op = cols * (long long)(s->dev.nz + 1);
+    const long long pw = (s->nn + kPwChunk - 1) / kPwChunk;
+    cap_op += op;
+    cap_pw += pw;
+    cap_partial += std::max(op, pw);
   }
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e->grid = (int)std::max(1LL, std::min(tiles, (long long)sms * 8));
+  if (cap_op > (1LL << 30) || cap_pw > (1LL << 30)) {
+    delete e;
+    return set_error(HEAT_ERR_ARG, "engine: too many work items");
+  }
+  e->cap_op = cap_op;
+  e->cap_pw = cap_pw;
+  e->cap_partial = cap_partial;
   heat_status st = HEAT_OK;
   auto fail = [&](heat_status s) {
     engine_destroy(e);
     return s;
   };
   if (cudaMalloc(&e->d_sims, sizeof(SimDev) * nsims) != cudaSuccess ||
-      cudaMalloc(&e->d_work, sizeof(int2) * tiles) != cudaSuccess ||
-      cudaMalloc(&e->d_nwork, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_work_op, sizeof(int2) * cap_op) != cudaSuccess ||
+      cudaMalloc(&e->d_work_pw, sizeof(int2) * cap_pw) != cudaSuccess ||
+      cudaMalloc(&e->d_nwork, sizeof(int) * 2) != cudaSuccess ||
       cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&e->d_partial, sizeof(double) * 4 * tiles) != cudaSuccess ||
+      cudaMalloc(&e->d_partial, sizeof(double) * 4 * cap_partial) != cudaSuccess ||
       cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_error(HEAT_ERR_NOMEM, "engine: device allocation failed"));
@@ -193,7 +233,8 @@ void engine_destroy(Engine* e) {
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   if (e->graph) cudaGraphDestroy(e->graph);
   cudaFree(e->d_sims);
-  cudaFree(e->d_work);
+  cudaFree(e->d_work_op);
+  cudaFree(e->d_work_pw);
   cudaFree(e->d_nwork);
   cudaFree(e->d_unfinished);
   cudaFree(e->d_partial);
@@ -201,7 +242,11 @@ void engine_destroy(Engine* e) {
   delete e;
 }
 
-heat_status engine_refresh(Engine* e) { return engine_upload(e); }
+heat_status engine_refresh(Engine* e) {
+  heat_status st = engine_upload(e);
+  if (st != HEAT_OK) return st;
+  return engine_capture(e);  // grids may have changed
+}
 
 heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters) {
   int max_iter = 1, max_outer = 1, poll = 32;
@@ -271,10 +316,20 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
   return first_bad;
 }
 
+// Reads a buffer larger than L2 so the next kernel starts cold. Reading (not
+// writing) leaves clean lines, so no write-back lands in the timed kernel.
+__global__ void k_flush_read(const uint4* __restrict__ p, size_t n, unsigned int* sink) {
+  unsigned int acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint4 v = __ldcg(p + i);
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x9e3779b9u) *sink = acc;  // keeps the loads alive; practically never taken
+}
+
 heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
                            double* ms_update, double* bytes_apply, double* bytes_update) {
   heat_sim* s = e->sims[0];
-  const int block = e->ks.tx * e->ks.ty;
   const int chunk = 40;  // below the inner-solve cap and the true-residual period
   cudaEvent_t ev[4 * chunk];
   for (int i = 0; i < 4 * chunk; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
@@ -296,13 +351,13 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
     st = sim_write_scalars(s);
     if (st != HEAT_OK) break;
     for (int i = 0; i < c; ++i) {
-      if (flush) cudaMemsetAsync(flush, i & 0xff, flush_bytes, e->stream);
+      if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
       cudaEventRecord(ev[4 * i + 0], e->stream);
-      e->ks.apply<<<e->grid, block, 0, e->stream>>>(e->d_sims, e->d_work, e->d_nwork);
+      e->ks.apply<<<e->grid_op, e->ks.apply_threads, 0, e->stream>>>(e->d_sims, e->d_work_op, e->d_nwork);
       cudaEventRecord(ev[4 * i + 1], e->stream);
-      if (flush) cudaMemsetAsync(flush, (i + 1) & 0xff, flush_bytes, e->stream);
+      if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
       cudaEventRecord(ev[4 * i + 2], e->stream);
-      e->ks.update<<<e->grid, block, 0, e->stream>>>(e->d_sims, e->d_work, e->d_nwork);
+      e->ks.update<<<e->grid_pw, kPwThreads, 0, e->stream>>>(e->d_sims, e->d_work_pw, e->d_nwork + 1);
       cudaEventRecord(ev[4 * i + 3], e->stream);
     }
     if (cudaStreamSynchronize(e->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -330,7 +385,7 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   for (heat_sim* x : e->sims) {
     const double n = (double)x->nn, ne = (double)x->ne;
     if (e->prec == P_FP64) {
-      ba += n * (3 * 8 + 2 * 8) + ne * 16;  // r, P^-1, d_old in; d, q out; (rho_c, k)
+      ba += n * (3 * 8 + 2 * 8) + ne * 16;    // r, P^-1, d_old in; d, q out; (rho_c, k)
       bu += n * (2 * 8 + 8 + 2 * 8 + 8 + 8);  // x in/out, d, r in/out, q, P^-1
     } else {
       ba += n * (3 * 4 + 2 * 4) + ne * 8;

@@ -39,6 +39,8 @@ namespace heat {
 heat_status set_error(heat_status st, const char* fmt, ...);
 // Q1 element mass/stiffness entries of an hx*hy*hz box by corner XOR pattern.
 void element_classes(double hx, double hy, double hz, double mhat[8], double khat[8]);
+// The same element matrices' eigenvalues in the corners' Walsh basis, / 8.
+void walsh_eigenvalues(double hx, double hy, double hz, double lam_m[8], double lam_k[8]);
 heat_status sim_alloc(heat_sim* s, void** p, size_t bytes);
 heat_status sim_upload_desc(heat_sim* s);
 heat_status sim_read_scalars(heat_sim* s);

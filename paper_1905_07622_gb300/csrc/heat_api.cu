@@ -67,7 +67,9 @@ extern "C" heat_status heat_create_mesh(int nx, int ny, int nz, const double ori
   if (nx < 1 || ny < 1 || nz < 1)
     return set_error(HEAT_ERR_ARG, "heat_create_mesh: nx, ny, nz must be >= 1 (got %d %d %d)", nx, ny, nz);
   const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
-  if (nn > (1LL << 40)) return set_error(HEAT_ERR_ARG, "heat_create_mesh: mesh too large");
+  // node and element indices are 32-bit in the kernels
+  if (nn >= (1LL << 31) - 1)
+    return set_error(HEAT_ERR_ARG, "heat_create_mesh: %lld nodes; at most 2^31 - 2 per mesh", nn);
   heat_mesh* m = new heat_mesh();
   m->nx = nx;
   m->ny = ny;
@@ -108,6 +110,25 @@ void heat::element_classes(double hx, double hy, double hz, double mhat[8], doub
     }
     mhat[p] = m[0] * m[1] * m[2];
     khat[p] = kk[0] * m[1] * m[2] + m[0] * kk[1] * m[2] + m[0] * m[1] * kk[2];
+  }
+}
+
+// Eigenvalues of the same element matrices in the Walsh basis of the corners
+// (w = wx | wy<<1 | wz<<2; w_d = 0: sum, 1: difference): in 1-D the mass
+// h/6*[2 1;1 2] has eigenvalues h/2 (sum) and h/6 (difference), the stiffness
+// 1/h*[1 -1;-1 1] has 0 and 2/h. Divided by 8, the normalisation of the
+// inverse 3-D transform.
+void heat::walsh_eigenvalues(double hx, double hy, double hz, double lam_m[8], double lam_k[8]) {
+  const double h[3] = {hx, hy, hz};
+  for (int w = 0; w < 8; ++w) {
+    double m[3], kk[3];
+    for (int d = 0; d < 3; ++d) {
+      const bool diff = (w >> d) & 1;
+      m[d] = diff ? h[d] / 6.0 : h[d] / 2.0;
+      kk[d] = diff ? 2.0 / h[d] : 0.0;
+    }
+    lam_m[w] = m[0] * m[1] * m[2] / 8.0;
+    lam_k[w] = (kk[0] * m[1] * m[2] + m[0] * kk[1] * m[2] + m[0] * m[1] * kk[2]) / 8.0;
   }
 }
 
@@ -240,9 +261,12 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   for (int f = 0; f < 6; ++f) d.g[f] = b.dirichlet_value[f];
   const double hx = mesh->extent[0] / mesh->nx, hy = mesh->extent[1] / mesh->ny, hz = mesh->extent[2] / mesh->nz;
   element_classes(hx, hy, hz, d.mhat, d.khat);
+  walsh_eigenvalues(hx, hy, hz, d.lam_m, d.lam_k);
   for (int p = 0; p < 8; ++p) {
     d.mhat_f[p] = (float)d.mhat[p];
     d.khat_f[p] = (float)d.khat[p];
+    d.lam_m_f[p] = (float)d.lam_m[p];
+    d.lam_k_f[p] = (float)d.lam_k[p];
   }
   fill_params(s);
 

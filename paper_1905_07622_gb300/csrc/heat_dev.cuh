@@ -16,7 +16,8 @@ enum Phase : int {
   PH_ITER = 2,    // CG iterations (FP64, or FP32 inner solve)
   PH_OUTER = 3,   // FP32 path: x64 += e, FP64 true residual, restart inner
   PH_DONE = 4,    // target step reached
-  PH_FAILED = 5   // status holds the error
+  PH_FAILED = 5,  // status holds the error
+  PH_RESID = 6    // FP64 path: true residual r = b - A x (every resid_period iterations)
 };
 
 enum Prec : int { P_FP64 = 0, P_FP32_REFINED = 1, P_FP32_PLAIN = 2 };
@@ -54,9 +55,11 @@ struct SimScalars {
   long long steps_total;
 };
 
-struct SimDev {
+struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   int nx, ny, nz;             // elements per dimension
-  int ntx, nty, ntz, ntiles;  // tiles of the tile kernels
+  int ntx, nty, ntz, ntiles;  // operator tiles (x, y, z counts and total)
+  int tz_len;                 // node levels per operator tile
+  int npw;                    // pointwise chunks (kPwChunk nodes each)
   long long nn;               // nodes
   uint32_t dir_faces;         // Dirichlet face bits
   int prec;                   // Prec
@@ -65,6 +68,12 @@ struct SimDev {
   double inv_dt, theta, rtol, inner_rtol;
   double mhat[8], khat[8];    // element mass/stiffness entry by corner XOR pattern
   float mhat_f[8], khat_f[8];
+  // Eigenvalues of the element mass and stiffness matrices in the element's
+  // Walsh basis (index w = wx | wy<<1 | wz<<2), divided by 8 (the inverse
+  // transform's normalisation): lam_m[w] = prod_d (w_d ? h_d/6 : h_d/2) / 8,
+  // lam_k[w] = sum_d (w_d ? 2/h_d : 0) prod_{d' != d} (...) / 8.
+  double lam_m[8], lam_k[8];
+  float lam_m_f[8], lam_k_f[8];
   const double2* coef;        // (rho_c, k) per element
   const float2* coef32;
   double* vec64[4];           // U^{n-1}, U^{n-2}, x and spare (slots in SimScalars)

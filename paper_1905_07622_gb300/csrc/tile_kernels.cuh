@@ -1,73 +1,147 @@
-// Phase-gated tile kernels of the solver.
+// Phase-gated kernels of the solver (Algorithm 1, §3.3), driven by the tick
+// engine over work lists of (simulation, work item) pairs:
+//   k_open      [operator tiles] step start: b = L u^{n-1} + F^n - lift,
+//               x0 = 2u^{n-1} - u^{n-2}, r = b - A x0 (PH_OPEN); the FP64 true
+//               residual r = b - A x every resid_period iterations (PH_RESID);
+//               on the FP32 paths the refinement sweep x64 += e32,
+//               r = b - A x64 in FP64, inner restart (PH_OUTER).
+//   k_apply_dot [operator tiles] d = P^-1 r + beta d_old computed while staging
+//               (so the direction update has no kernel of its own), q = A' d,
+//               alpha = delta / d.q.
+//   k_update    [pointwise chunks] x += alpha d, r -= alpha q, delta = r.P^-1 r,
+//               beta, convergence, phase changes, step close.
+// Every reduction is a per-item partial summed in item order by the last
+// block of the simulation, so a simulation's result does not depend on what
+// else shares the launch.
 //
-// Operator: y_i = sum_{e containing i} sum_{j in e} (sa*rho_c_e*Mhat[c_i^c_j] +
-// sb*k_e*Khat[c_i^c_j]) x_j -- the assembly operator of §3.2 Eq. 1 read degree
-// of freedom by degree of freedom (each output node gathers from its <= 8
-// elements and 27 neighbours; no atomics, no assembled matrix). Mhat/Khat are
-// the Q1 element matrices indexed by the XOR of the two local corner numbers.
-//
-// Solver: Algorithm 1 (§3.3) split into three phase-gated tile kernels --
-//   k_open      step start (right-hand side, x0, r = b - A x0) and, on the
-//               FP32 paths, the FP64 refinement sweep (x += e, r = b - A x);
-//   k_apply_dot d = P^-1 r + beta d (computed on the fly, so the direction
-//               update needs no kernel of its own), q = A d, alpha = delta/(d.q);
-//   k_update    x += alpha d, r -= alpha q (or r = b - A x every resid_period
-//               iterations), delta = r.P^-1 r, beta, convergence, step close.
-// Every reduction is a per-tile partial summed in tile order by the last block
-// of the simulation, so results do not depend on what else shares a launch.
+// Each block keeps the descriptor and control scalars of the simulation it is
+// working on in shared memory, loaded once per simulation (a launch changes a
+// simulation's scalars only after all of its items are done), instead of every
+// warp re-reading them from L2.
 #pragma once
 
 #include "op.cuh"
 
 namespace heat {
 
-// ------------------------------------------------------ phase-gated tile kernels
+constexpr int kPwChunk = 1024;    // nodes per pointwise work item
+constexpr int kPwThreads = 256;   // 4 nodes per thread
 
-// Per-work-item control block, loaded by thread 0 into shared memory.
+// Control scalars of a simulation (written only by earlier kernels, or by
+// the last block after all of the simulation's items of this kernel).
 struct Ctl {
   int phase, iu1, iu2, ix, ixa, id, restart, have_prev, iter, step;
   double alpha, beta;
 };
 
-__device__ __forceinline__ void load_ctl(const SimScalars* sc, Ctl& c) {
-  const volatile SimScalars* v = sc;
-  c.phase = v->phase;
-  c.iu1 = v->iu1;
-  c.iu2 = v->iu2;
-  c.ix = v->ix;
-  c.ixa = v->ixa;
-  c.id = v->id;
-  c.restart = v->restart;
-  c.have_prev = v->have_prev;
-  c.iter = v->iter;
-  c.step = v->step;
-  c.alpha = v->alpha;
-  c.beta = v->beta;
+__device__ __forceinline__ Ctl load_ctl(const SimScalars* sc) {
+  Ctl c;
+  c.phase = __ldcg(&sc->phase);
+  c.iu1 = __ldcg(&sc->iu1);
+  c.iu2 = __ldcg(&sc->iu2);
+  c.ix = __ldcg(&sc->ix);
+  c.ixa = __ldcg(&sc->ixa);
+  c.id = __ldcg(&sc->id);
+  c.restart = __ldcg(&sc->restart);
+  c.have_prev = __ldcg(&sc->have_prev);
+  c.iter = __ldcg(&sc->iter);
+  c.step = __ldcg(&sc->step);
+  c.alpha = __ldcg(&sc->alpha);
+  c.beta = __ldcg(&sc->beta);
+  return c;
 }
 
-// Copy the work item's descriptor into shared memory (all threads), and the
-// control scalars (thread 0). Ends with a barrier.
-__device__ __forceinline__ void load_item(const SimDev* sims, int sim, SimDev& sh, Ctl& ctl) {
-  const int* src = reinterpret_cast<const int*>(&sims[sim]);
-  int* dst = reinterpret_cast<int*>(&sh);
-  for (int t = threadIdx.x; t < (int)(sizeof(SimDev) / sizeof(int)); t += blockDim.x) dst[t] = src[t];
+// Shared-memory copy of the current simulation's descriptor and scalars.
+struct ItemCache {
+  SimDev s;
+  Ctl c;
+};
+
+// Makes `cache` hold simulation `sim` (cur is the caller's register copy of
+// the cached id; every thread tracks the same sequence, so the branch is
+// uniform). Contains barriers when it reloads.
+__device__ __forceinline__ void cache_sim(const SimDev* __restrict__ sims, int sim, ItemCache& cache, int& cur) {
+  if (sim == cur) return;
+  __syncthreads();  // the previous simulation's users are done
+  if (threadIdx.x < 32) {
+    const uint4* src = reinterpret_cast<const uint4*>(&sims[sim]);
+    uint4* dst = reinterpret_cast<uint4*>(&cache.s);
+    for (int t = threadIdx.x; t < (int)(sizeof(SimDev) / sizeof(uint4)); t += 32) dst[t] = src[t];
+    __syncwarp();
+    if (threadIdx.x == 0) cache.c = load_ctl(cache.s.sc);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) load_ctl(sh.sc, ctl);
+  cur = sim;
+}
+
+// Block sum of per-thread partials of type T: each warp sums in T, the warp
+// sums are converted to FP64 and added by thread 0 in warp order. (On this
+// GPU FP64 runs at 1/58 of the FP32 rate, so FP64 work per thread would cost
+// more than the streaming it accompanies.) red: NV*32 doubles. Result in thread 0.
+template <class T, int NV>
+__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  T w[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    w[a] = v[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w[a] += __shfl_down_sync(0xffffffffu, w[a], o);
+  }
   __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * 32 + warp] = (double)w[a];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = 0.0;
+      for (int k = 0; k < nwarps; ++k) t += red[a * 32 + k];
+      out[a] = t;
+    }
+  }
 }
 
-__device__ __forceinline__ void tile_origin(const SimDev& s, int t, int TX, int TY, int TZ, int& i0,
-                                            int& j0, int& k0) {
-  const int tx = t % s.ntx;
-  const int r = t / s.ntx;
-  const int ty = r % s.nty;
-  const int tz = r / s.nty;
-  i0 = tx * TX;
-  j0 = ty * TY;
-  k0 = tz * TZ;
+// Publishes a work item's partials (per-thread values of type T). Warp 0
+// alone then takes the completion count; only the warp that finishes the
+// simulation's last item of this kernel sums all items' partials (in item
+// order) and returns true, with the totals in lane 0's out. The other warps
+// do not wait for the count.
+template <class T, int NV>
+__device__ __forceinline__ bool finish_item(const SimDev& s, int item, int nitems, const T (&v)[NV],
+                                            double (&out)[NV], double* red) {
+  block_sum_t<T, NV>(v, out, red);
+  if (threadIdx.x >= 32) return false;
+  int last = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s.partial[4 * item + a] = out[a];
+    __threadfence();
+    last = atomicAdd(&s.sc->count, 1u) == (unsigned int)(nitems - 1);
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return false;
+  __threadfence();
+  double t[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) t[a] = 0.0;
+  for (int u = threadIdx.x; u < nitems; u += 32) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) t[a] += __ldcg(&s.partial[4 * u + a]);
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[a] += __shfl_down_sync(0xffffffffu, t[a], o);
+    out[a] = t[a];  // valid in lane 0
+  }
+  return threadIdx.x == 0;
 }
 
-// Step close, run by thread 0 of the last block: log, rotate the state ring
+// Step close, run by one thread: log, rotate the state ring
 // (U^{n-2} <- U^{n-1} <- x; the old U^{n-2} slot becomes the next x).
 __device__ __forceinline__ void close_step(const SimDev& s, SimScalars* sc, double delta_final) {
   const int st = sc->step;
@@ -92,106 +166,156 @@ __device__ __forceinline__ void fail(SimScalars* sc, int status) {
   sc->phase = PH_FAILED;
 }
 
-// k_open: PH_OPEN (all precisions) and PH_OUTER (FP32 paths).
-template <int P, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX* TY) k_open(const SimDev* __restrict__ sims, const int2* __restrict__ work,
+struct TileCoords {
+  int i0, j0, k0, nzt;
+};
+
+template <int SX, int SY>
+__device__ __forceinline__ TileCoords tile_coords(const SimDev& s, int t) {
+  const int tx = t % s.ntx;
+  const int r = t / s.ntx;
+  const int ty = r % s.nty;
+  const int tz = r / s.nty;
+  TileCoords c;
+  c.i0 = tx * (SX - 1);
+  c.j0 = ty * (SY - 1);
+  c.k0 = tz * s.tz_len;
+  c.nzt = min(s.tz_len, s.nz + 1 - c.k0);
+  return c;
+}
+
+// ------------------------------------------------------------------ k_open
+
+struct D2 {
+  double a, b;
+};
+
+template <int P, int SX, int SY>
+__global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                  const int* __restrict__ nwork_p) {
-  __shared__ SimDev s;
-  __shared__ Ctl ctl;
+  __shared__ TileSmem<double, SX, SY> sh;
   __shared__ double red[3 * 32];
-  __shared__ int s_last;
+  __shared__ ItemCache cache;
+  int cur = -1;
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    load_item(sims, wi.x, s, ctl);
-    const int phase = ctl.phase;
-    if (phase != PH_OPEN && !(P != P_FP64 && phase == PH_OUTER)) {
-      __syncthreads();
-      continue;
+    cache_sim(sims, wi.x, cache, cur);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    const int phase = c.phase;
+    const bool act = phase == PH_OPEN || (P != P_FP64 && phase == PH_OUTER) || (P == P_FP64 && phase == PH_RESID);
+    if (!act) continue;
+    const Geo g(s);
+    const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
+    const double* __restrict__ pinv = s.pinv;
+    double* __restrict__ b = s.b;
+    double part[3] = {0.0, 0.0, 0.0};  // r.P^-1 r (FP64), b.P^-1 b, r32.P^-1 r32
+    const double inv_dt = s.inv_dt, theta = s.theta;
+    // value of a Dirichlet node from its index (faces only, so rarely called)
+    auto dval = [&](int m) -> double {
+      const int kk = m / g.pxy, rem = m - kk * g.pxy, jj = rem / g.px;
+      return dirichlet_value(s, rem - jj * g.px, jj, kk);
+    };
+    auto ident = [](double v) { return v; };
+    if (phase == PH_OPEN) {
+      const double* __restrict__ u1 = s.vec64[c.iu1];
+      const double* __restrict__ u2 = s.vec64[c.iu2];
+      double* __restrict__ x = s.vec64[c.ix];
+      const bool hp = c.have_prev != 0;
+      const bool flux_on = s.flux_steps < 0 || c.step + 1 <= s.flux_steps;
+      const double* __restrict__ F = s.F;
+      const double* __restrict__ lift = s.zlift;
+      // pass 1: b = L u^{n-1} + F^n - A_{.D} g (free rows), g (Dirichlet rows)
+      tile_op<double, SX, SY>(
+          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta - 1.0, false, sh,
+          [&](int m, bool live) -> double { return live ? u1[m] : 0.0; }, ident,
+          [&](int m, bool dir, double y, double) {
+            if (dir) {
+              b[m] = dval(m);
+            } else {
+              const double bn = y + (flux_on ? F[m] : 0.0) - lift[m];
+              b[m] = bn;
+              part[1] += bn * bn * pinv[m];
+            }
+          });
+      // pass 2: x0 = 2u^{n-1} - u^{n-2} (u^{n-1} on the first step), r = b - A' x0
+      tile_op<double, SX, SY>(
+          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
+          [&](int m, bool live) -> D2 {
+            if (!live) return {0.0, 0.0};
+            return {u1[m], hp ? u2[m] : u1[m]};
+          },
+          [](const D2& r) { return 2.0 * r.a - r.b; },
+          [&](int m, bool dir, double y, double v) {
+            double rn = 0.0;
+            if (dir) {
+              x[m] = dval(m);
+            } else {
+              x[m] = v;
+              rn = b[m] - y;
+            }
+            if (P == P_FP64) {
+              s.r[m] = rn;
+            } else {
+              const float r32 = (float)rn;
+              s.r32[m] = r32;
+              part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+            }
+            part[0] += rn * rn * pinv[m];
+          });
+    } else if (phase == PH_OUTER) {
+      // x64 <- x64 + e32 (into the spare slot), r = b - A' x64 in FP64
+      const double* __restrict__ x = s.vec64[c.ix];
+      double* __restrict__ xa = s.vec64[c.ixa];
+      const float* __restrict__ e32 = s.e32;
+      tile_op<double, SX, SY>(
+          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
+          [&](int m, bool live) -> D2 {
+            if (!live) return {0.0, 0.0};
+            return {x[m], (double)e32[m]};
+          },
+          [](const D2& r) { return r.a + r.b; },
+          [&](int m, bool dir, double y, double v) {
+            double rn = 0.0;
+            if (dir) {
+              xa[m] = dval(m);
+            } else {
+              xa[m] = v;
+              rn = b[m] - y;
+            }
+            const float r32 = (float)rn;
+            s.r32[m] = r32;
+            part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+            part[0] += rn * rn * pinv[m];
+          });
+    } else {  // PH_RESID (FP64): r = b - A' x, x already advanced by k_update
+      const double* __restrict__ x = s.vec64[c.ix];
+      double* __restrict__ r = s.r;
+      tile_op<double, SX, SY>(
+          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
+          [&](int m, bool live) -> double { return live ? x[m] : 0.0; }, ident,
+          [&](int m, bool dir, double y, double) {
+            const double rn = dir ? 0.0 : b[m] - y;
+            r[m] = rn;
+            part[0] += rn * rn * pinv[m];
+          });
     }
-    int i0, j0, k0;
-    tile_origin(s, wi.y, TX, TY, TZ, i0, j0, k0);
-    const int i = i0 + (int)(threadIdx.x % TX), j = j0 + (int)(threadIdx.x / TX);
-    double part[3] = {0.0, 0.0, 0.0};  // r.P^-1 r (FP64), b.P^-1 b, inner r32.P^-1 r32
-    const double* u1 = s.vec64[ctl.iu1];
-    const double* u2 = s.vec64[ctl.iu2];
-    double* x = s.vec64[ctl.ix];
-    double* xa = s.vec64[ctl.ixa];
-    const bool hp = ctl.have_prev != 0;
-    const bool flux_on = s.flux_steps < 0 || ctl.step + 1 <= s.flux_steps;
-    if (i <= s.nx && j <= s.ny) {
-      for (int kz = 0; kz < TZ; ++kz) {
-        const int k = k0 + kz;
-        if (k > s.nz) break;
-        const long long n = node_index(s, i, j, k);
-        const bool dir = is_dirichlet(s, i, j, k);
-        double rn = 0.0, bn;
-        if (phase == PH_OPEN) {
-          auto x0 = [&](int a, int b, int c) -> double {
-            if (is_dirichlet(s, a, b, c)) return 0.0;
-            const long long m = node_index(s, a, b, c);
-            return hp ? 2.0 * u1[m] - u2[m] : u1[m];
-          };
-          if (dir) {
-            bn = dirichlet_value(s, i, j, k);
-            x[n] = bn;
-          } else {
-            const double lu = gather_apply<double>(
-                s, s.inv_dt, s.theta - 1.0, i, j, k,
-                [&](int a, int b, int c) -> double { return u1[node_index(s, a, b, c)]; });
-            bn = lu + (flux_on ? s.F[n] : 0.0) - s.zlift[n];
-            rn = bn - gather_apply<double>(s, s.inv_dt, s.theta, i, j, k, x0);
-            x[n] = x0(i, j, k);
-          }
-          s.b[n] = bn;
-          if (!dir) part[1] += bn * bn * s.pinv[n];
-        } else {  // PH_OUTER: x <- x + e, r = b - A x
-          auto xe = [&](int a, int b, int c) -> double {
-            if (is_dirichlet(s, a, b, c)) return 0.0;
-            const long long m = node_index(s, a, b, c);
-            return x[m] + (double)s.e32[m];
-          };
-          if (dir) {
-            xa[n] = dirichlet_value(s, i, j, k);
-          } else {
-            rn = s.b[n] - gather_apply<double>(s, s.inv_dt, s.theta, i, j, k, xe);
-            xa[n] = xe(i, j, k);
-          }
-        }
-        if (P == P_FP64) {
-          s.r[n] = rn;
-        } else {
-          const float r32 = (float)rn;
-          s.r32[n] = r32;
-          part[2] += (double)r32 * (double)r32 * (double)s.pinv32[n];
-        }
-        part[0] += rn * rn * s.pinv[n];
-      }
-    }
-    block_sum<3>(part, red);
-    bool last = false;
-    if (threadIdx.x == 0) {
-      s.partial[4 * wi.y + 0] = part[0];
-      s.partial[4 * wi.y + 1] = part[1];
-      s.partial[4 * wi.y + 2] = part[2];
-      __threadfence();
-      const unsigned int done = atomicAdd(&s.sc->count, 1u);
-      last = (done == (unsigned int)(s.ntiles - 1));
-      s_last = last;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double tot[3] = {0.0, 0.0, 0.0};
-      for (int t = threadIdx.x; t < s.ntiles; t += blockDim.x) {
-        tot[0] += __ldcg(&s.partial[4 * t + 0]);
-        tot[1] += __ldcg(&s.partial[4 * t + 1]);
-        tot[2] += __ldcg(&s.partial[4 * t + 2]);
-      }
-      block_sum<3>(tot, red);
-      if (threadIdx.x == 0) {
-        SimScalars* sc = s.sc;
-        sc->count = 0;
+    double tot[3];
+    if (finish_item<double, 3>(s, wi.y, s.ntiles, part, tot, red)) {
+      SimScalars* sc = s.sc;
+      sc->count = 0;
+      if (phase == PH_RESID) {
+        const double dn = tot[0];
+        sc->beta = dn / sc->delta;
+        sc->delta = dn;
+        sc->iter += 1;
+        sc->iter_step += 1;
+        if (!isfinite(dn)) fail(sc, ST_NONFINITE);
+        else if (dn <= sc->thresh) close_step(s, sc, dn);
+        else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
+        else sc->phase = PH_ITER;
+      } else {
         if (phase == PH_OPEN) {
           sc->delta_b = tot[1];
           sc->thresh = s.rtol * s.rtol * tot[1];
@@ -206,7 +330,7 @@ __global__ void __launch_bounds__(TX* TY) k_open(const SimDev* __restrict__ sims
         }
         sc->iter = 0;
         sc->restart = 1;
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
           fail(sc, ST_NONFINITE);
         } else if (P == P_FP64) {
           sc->delta = tot[0];
@@ -227,194 +351,188 @@ __global__ void __launch_bounds__(TX* TY) k_open(const SimDev* __restrict__ sims
         }
       }
     }
-    __syncthreads();
   }
 }
 
-// T = double: the FP64 path; T = float: the FP32 inner solve.
+// ------------------------------------------------------------- k_apply_dot
+
 template <class T> struct IterVecs;
 template <> struct IterVecs<double> {
   __device__ static const double* r(const SimDev& s) { return s.r; }
   __device__ static const double* pinv(const SimDev& s) { return s.pinv; }
   __device__ static double* d(const SimDev& s, int id) { return s.d[id]; }
   __device__ static double* q(const SimDev& s) { return s.q; }
+  __device__ static const double2* coef(const SimDev& s) { return s.coef; }
 };
 template <> struct IterVecs<float> {
   __device__ static const float* r(const SimDev& s) { return s.r32; }
   __device__ static const float* pinv(const SimDev& s) { return s.pinv32; }
   __device__ static float* d(const SimDev& s, int id) { return s.d32[id]; }
   __device__ static float* q(const SimDev& s) { return s.q32; }
+  __device__ static const float2* coef(const SimDev& s) { return s.coef32; }
 };
 
-// k_apply_dot: d = P^-1 r + beta d_old (beta = 0 after a restart), q = A' d, d.q.
-template <class T, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX* TY) k_apply_dot(const SimDev* __restrict__ sims, const int2* __restrict__ work,
+template <class T>
+struct DirRaw {
+  T p, r, d;
+};
+
+template <class T, int SX, int SY>
+__global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                       const int* __restrict__ nwork_p) {
-  __shared__ SimDev s;
-  __shared__ Ctl ctl;
+  __shared__ TileSmem<T, SX, SY> sh;
   __shared__ double red[32];
-  __shared__ int s_last;
+  __shared__ ItemCache cache;
+  int cur = -1;
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    load_item(sims, wi.x, s, ctl);
-    if (ctl.phase != PH_ITER) {
-      __syncthreads();
-      continue;
-    }
-    int i0, j0, k0;
-    tile_origin(s, wi.y, TX, TY, TZ, i0, j0, k0);
-    const int i = i0 + (int)(threadIdx.x % TX), j = j0 + (int)(threadIdx.x / TX);
-    const T* r = IterVecs<T>::r(s);
-    const T* pinv = IterVecs<T>::pinv(s);
-    const T* dold = IterVecs<T>::d(s, ctl.id);
-    T* dnew = IterVecs<T>::d(s, ctl.id ^ 1);
-    T* q = IterVecs<T>::q(s);
-    const bool rs = ctl.restart != 0;
-    const T beta = (T)ctl.beta;
-    auto dl = [&](int a, int b, int c) -> T {
-      if (is_dirichlet(s, a, b, c)) return T(0);
-      const long long m = node_index(s, a, b, c);
-      const T sv = pinv[m] * r[m];
-      return rs ? sv : sv + beta * dold[m];
-    };
-    double part[1] = {0.0};
-    if (i <= s.nx && j <= s.ny) {
-      for (int kz = 0; kz < TZ; ++kz) {
-        const int k = k0 + kz;
-        if (k > s.nz) break;
-        const long long n = node_index(s, i, j, k);
-        if (is_dirichlet(s, i, j, k)) {
-          dnew[n] = T(0);
-          q[n] = T(0);
-          continue;
-        }
-        const T qn = gather_apply<T>(s, (T)s.inv_dt, (T)s.theta, i, j, k, dl);
-        const T dn = dl(i, j, k);
-        dnew[n] = dn;
-        q[n] = qn;
-        part[0] += (double)dn * (double)qn;
+    cache_sim(sims, wi.x, cache, cur);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    if (c.phase != PH_ITER) continue;
+    const Geo g(s);
+    const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
+    const T* __restrict__ r = IterVecs<T>::r(s);
+    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+    const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
+    T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
+    T* __restrict__ q = IterVecs<T>::q(s);
+    const bool rs = c.restart != 0;
+    const T beta = rs ? T(0) : (T)c.beta;
+    // Per-thread partial in T (FP32 on the FP32 path), FP64 from the warp sums on.
+    T acc = T(0);
+    tile_op<T, SX, SY>(
+        g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
+        [&](int m, bool live) -> DirRaw<T> {
+          if (!live) return {T(0), T(0), T(0)};
+          return {pinv[m], r[m], rs ? T(0) : dold[m]};
+        },
+        [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; },
+        [&](int m, bool dir, T y, T v) {
+          const T qv = dir ? T(0) : y;
+          q[m] = qv;
+          dnew[m] = v;
+          acc += v * qv;
+        });
+    const T accv[1] = {acc};
+    double tot[1];
+    if (finish_item<T, 1>(s, wi.y, s.ntiles, accv, tot, red)) {
+      SimScalars* sc = s.sc;
+      sc->count = 0;
+      const double dq = tot[0];
+      sc->dq = dq;
+      if (!isfinite(dq)) fail(sc, ST_NONFINITE);
+      else if (!(dq > 0.0)) fail(sc, ST_BREAKDOWN);
+      else {
+        sc->alpha = sc->delta / dq;
+        sc->id ^= 1;
+        sc->restart = 0;
       }
     }
-    block_sum<1>(part, red);
-    if (threadIdx.x == 0) {
-      s.partial[4 * wi.y] = part[0];
-      __threadfence();
-      const unsigned int done = atomicAdd(&s.sc->count, 1u);
-      s_last = (done == (unsigned int)(s.ntiles - 1));
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double tot[1] = {0.0};
-      for (int t = threadIdx.x; t < s.ntiles; t += blockDim.x) tot[0] += __ldcg(&s.partial[4 * t]);
-      block_sum<1>(tot, red);
-      if (threadIdx.x == 0) {
-        SimScalars* sc = s.sc;
-        sc->count = 0;
-        const double dq = tot[0];
-        sc->dq = dq;
-        if (!isfinite(dq)) fail(sc, ST_NONFINITE);
-        else if (!(dq > 0.0)) fail(sc, ST_BREAKDOWN);
-        else {
-          sc->alpha = sc->delta / dq;
-          sc->id ^= 1;
-          sc->restart = 0;
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
-// k_update: x += alpha d, r -= alpha q (r = b - A x on true-residual
-// iterations of the FP64 path), delta_new = r.P^-1 r, beta, convergence.
-template <class T, int P, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX* TY) k_update(const SimDev* __restrict__ sims, const int2* __restrict__ work,
-                                                   const int* __restrict__ nwork_p) {
-  __shared__ SimDev s;
-  __shared__ Ctl ctl;
+// ---------------------------------------------------------------- k_update
+
+// Four consecutive node values (a float4, or two double2).
+template <class T> struct Quad;
+template <> struct Quad<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ void store(float* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Quad<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+template <class T, int P>
+__global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict__ sims, const int2* __restrict__ work,
+                                                       const int* __restrict__ nwork_p) {
   __shared__ double red[32];
-  __shared__ int s_last;
+  __shared__ ItemCache cache;
+  int cur = -1;
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    load_item(sims, wi.x, s, ctl);
-    if (ctl.phase != PH_ITER) {
-      __syncthreads();
-      continue;
-    }
-    const bool resid = (P == P_FP64) && s.resid_period > 0 && ctl.iter > 0 && (ctl.iter % s.resid_period) == 0;
-    int i0, j0, k0;
-    tile_origin(s, wi.y, TX, TY, TZ, i0, j0, k0);
-    const int i = i0 + (int)(threadIdx.x % TX), j = j0 + (int)(threadIdx.x / TX);
-    T* r = const_cast<T*>(IterVecs<T>::r(s));
-    const T* pinv = IterVecs<T>::pinv(s);
-    const T* d = IterVecs<T>::d(s, ctl.id);
-    const T* q = IterVecs<T>::q(s);
-    const T alpha = (T)ctl.alpha;
-    const bool first = ctl.iter == 0;
-    double part[1] = {0.0};
-    if (i <= s.nx && j <= s.ny) {
-      for (int kz = 0; kz < TZ; ++kz) {
-        const int k = k0 + kz;
-        if (k > s.nz) break;
-        const long long n = node_index(s, i, j, k);
-        T rn;
-        if constexpr (P == P_FP64) {
-          double* x = s.vec64[ctl.ix];
-          if (!resid) {
-            x[n] += alpha * d[n];
-            rn = r[n] - alpha * q[n];
-          } else {
-            double* xa = s.vec64[ctl.ixa];
-            if (is_dirichlet(s, i, j, k)) {
-              xa[n] = dirichlet_value(s, i, j, k);
-              rn = 0.0;
-            } else {
-              auto xl = [&](int a, int b, int c) -> double {
-                if (is_dirichlet(s, a, b, c)) return 0.0;
-                const long long m = node_index(s, a, b, c);
-                return x[m] + alpha * d[m];
-              };
-              rn = s.b[n] - gather_apply<double>(s, s.inv_dt, s.theta, i, j, k, xl);
-              xa[n] = xl(i, j, k);
-            }
-          }
+    cache_sim(sims, wi.x, cache, cur);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    if (c.phase != PH_ITER) continue;
+    const bool resid_it = (P == P_FP64) && s.resid_period > 0 && c.iter > 0 && (c.iter % s.resid_period) == 0;
+    const int nn = (int)s.nn;
+    const int base = wi.y * kPwChunk;
+    const int end = min(base + kPwChunk, nn);
+    T* __restrict__ x = (P == P_FP64) ? reinterpret_cast<T*>(s.vec64[c.ix]) : reinterpret_cast<T*>(s.e32);
+    T* __restrict__ r = const_cast<T*>(IterVecs<T>::r(s));
+    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+    const T* __restrict__ d = IterVecs<T>::d(s, c.id);
+    const T* __restrict__ q = IterVecs<T>::q(s);
+    const T alpha = (T)c.alpha;
+    const bool zero_x = (P != P_FP64) && c.iter == 0;  // the inner solve starts from e = 0
+    T part[1] = {T(0)};  // per-thread partial in T, FP64 from the warp sums on
+    for (int n = base + 4 * (int)threadIdx.x; n < end; n += 4 * (int)blockDim.x) {
+      if (n + 3 < end) {
+        Quad<T> xv, dv, rv, qv, pv;
+        dv.load(d + n);
+        if (zero_x) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) xv.v[a] = T(0);
         } else {
-          s.e32[n] = (first ? 0.0f : s.e32[n]) + alpha * d[n];
-          rn = r[n] - alpha * q[n];
+          xv.load(x + n);
         }
-        r[n] = rn;
-        part[0] += (double)rn * (double)rn * (double)pinv[n];
+        if (!resid_it) {
+          rv.load(r + n);
+          qv.load(q + n);
+          pv.load(pinv + n);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv.v[a] += alpha * dv.v[a];
+        xv.store(x + n);
+        if (!resid_it) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            rv.v[a] -= alpha * qv.v[a];
+            part[0] += rv.v[a] * rv.v[a] * pv.v[a];
+          }
+          rv.store(r + n);
+        }
+      } else {
+        for (int m = n; m < end; ++m) {
+          x[m] = (zero_x ? T(0) : x[m]) + alpha * d[m];
+          if (!resid_it) {
+            const T rn = r[m] - alpha * q[m];
+            r[m] = rn;
+            part[0] += rn * rn * pinv[m];
+          }
+        }
       }
     }
-    block_sum<1>(part, red);
-    if (threadIdx.x == 0) {
-      s.partial[4 * wi.y] = part[0];
-      __threadfence();
-      const unsigned int done = atomicAdd(&s.sc->count, 1u);
-      s_last = (done == (unsigned int)(s.ntiles - 1));
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double tot[1] = {0.0};
-      for (int t = threadIdx.x; t < s.ntiles; t += blockDim.x) tot[0] += __ldcg(&s.partial[4 * t]);
-      block_sum<1>(tot, red);
-      if (threadIdx.x == 0) {
-        SimScalars* sc = s.sc;
-        sc->count = 0;
-        const double dn = tot[0];
+    double pd[1];
+    if (finish_item<T, 1>(s, wi.y, s.npw, part, pd, red)) {
+      SimScalars* sc = s.sc;
+      sc->count = 0;
+      if (resid_it) {
+        sc->phase = PH_RESID;  // k_open recomputes r = b - A x and finishes the iteration
+      } else {
+        const double dn = pd[0];
         sc->beta = dn / sc->delta;
         sc->delta = dn;
         sc->iter += 1;
         sc->iter_step += 1;
-        if (resid) {
-          const int t2 = sc->ix;
-          sc->ix = sc->ixa;
-          sc->ixa = t2;
-        }
         if (!isfinite(dn)) {
           fail(sc, ST_NONFINITE);
         } else if (P == P_FP64) {
@@ -422,12 +540,11 @@ __global__ void __launch_bounds__(TX* TY) k_update(const SimDev* __restrict__ si
           else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
         } else {
           const int cap = (P == P_FP32_PLAIN) ? s.max_iter : s.resid_period;
-          if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
           if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
+          else if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
         }
       }
     }
-    __syncthreads();
   }
 }
 

@@ -145,6 +145,25 @@ heat_status heat_solve_transient(heat_sim* sim, int nsteps, double* u_out,
  * last heat_step call); iters may be NULL. */
 heat_status heat_step_iterations(heat_sim* sim, int s, int* iters);
 
+/* ---- batches --------------------------------------------------------------
+ * Many independent simulations advanced together (the paper's inverse
+ * problem runs thousands of forward solves on one precomputed mesh geometry
+ * with varying coefficients, §3.2, §5.3). Every kernel launch of a batch step
+ * carries all member simulations: sizes, coefficients, boundary conditions
+ * and iteration counts may all differ. Each member's reductions run in the
+ * same order as when it is stepped alone, so its results are bitwise
+ * identical to heat_step on the same simulation.
+ *   sims: nsims >= 1 distinct simulations with the same precision; they stay
+ *     owned by the caller and must not be stepped otherwise (or destroyed)
+ *     while the batch exists.
+ *   cuda_stream: stream of the batch's work (NULL: legacy default stream).
+ * heat_batch_step advances every member by nsteps steps; stats (nsims entries,
+ * or NULL) receives per-member statistics. It returns the first failing
+ * member's status; the other members complete their steps. */
+heat_status heat_batch_create(heat_sim* const* sims, int nsims, void* cuda_stream, heat_batch** out);
+heat_status heat_batch_step(heat_batch* batch, int nsteps, heat_step_stats* stats);
+void heat_destroy_batch(heat_batch* batch);
+
 /* ---- operator-level entry points (device pointers, sim stream) ---------- */
 
 /* y = A' x with A = M/dt + theta K (§3.2: A = M + theta dt K scaled by 1/dt),

@@ -83,6 +83,9 @@ _SIGS = [
     ("heat_diagonal", C.c_int, [_VP, _VP]),
     ("heat_rhs", C.c_int, [_VP, C.c_int, _VP, _VP]),
     ("heat_flux_vector", C.c_int, [_VP, _VP]),
+    ("heat_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, _VP, C.POINTER(_VP)]),
+    ("heat_batch_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
+    ("heat_destroy_batch", None, [_VP]),
     ("heat_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
     ("heat_apply_dot_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, _DP, C.c_double, C.c_double, C.c_uint32,
                                          _VP, _VP, _VP, _VP, _VP]),
@@ -290,6 +293,28 @@ def heat_profile_iteration(sim, reps: int, flush=None):
     fb = flush.numel() * flush.element_size() if flush is not None else 0
     _check(_lib.heat_profile_iteration(sim, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba), C.byref(bu)))
     return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_batch_create(sims, stream=None):
+    """A batch over simulation handles (c_void_p); the sims stay the caller's."""
+    load_library()
+    arr = (C.c_void_p * len(sims))(*[s.value if isinstance(s, C.c_void_p) else s for s in sims])
+    out = C.c_void_p()
+    st = C.c_void_p(int(stream) if stream else 0)
+    _check(_lib.heat_batch_create(arr, len(sims), st, C.byref(out)))
+    return out
+
+
+def heat_batch_step(batch, nsteps: int, nsims: int):
+    """Advance every member; returns (status, [per-member stats dicts])."""
+    stats = (heat_step_stats * nsims)()
+    rc = _lib.heat_batch_step(batch, int(nsteps), stats)
+    return rc, [s.as_dict() for s in stats]
+
+
+def heat_destroy_batch(batch):
+    if batch:
+        _lib.heat_destroy_batch(batch)
 
 
 def heat_apply_dot_noalloc(nx, ny, nz, extent, dt, theta, dirichlet_faces, coef, x, y, xdoty, stream=None):

@@ -79,14 +79,18 @@ struct Engine {
 
 // Operator tile geometry of one simulation: (SX-1) x (SY-1) node columns per
 // tile, tz_len levels. tz_len trades z-halo work (3 extra levels per tile)
-// against the number of tiles; aim for at least `want` tiles in total.
-static void tile_geometry(SimDev& d, const KernelSet& ks, long long want_tiles_this_sim) {
+// against the number of tiles. It depends on the simulation's own mesh only
+// (about kTileNodes output nodes per tile, at least 8 levels), so the tiles,
+// and with them the order of every reduction, are the same whether the
+// simulation runs alone or in a batch: its results are bitwise identical.
+constexpr long long kTileNodes = 2048;
+static void tile_geometry(SimDev& d, const KernelSet& ks) {
   d.ntx = (d.nx + 1 + ks.sx - 2) / (ks.sx - 1);
   d.nty = (d.ny + 1 + ks.sy - 2) / (ks.sy - 1);
   const int levels = d.nz + 1;
   const long long cols = (long long)d.ntx * d.nty;
-  int ntz = (int)std::max(1LL, std::min<long long>(levels, (want_tiles_this_sim + cols - 1) / cols));
-  // at least 8 levels per tile keeps the z-halo overhead below 40 %
+  const long long want = std::max(1LL, d.nn / kTileNodes);
+  int ntz = (int)std::max(1LL, std::min<long long>(levels, (want + cols - 1) / cols));
   ntz = std::min(ntz, std::max(1, levels / 8));
   d.tz_len = (levels + ntz - 1) / ntz;
   d.ntz = (levels + d.tz_len - 1) / d.tz_len;
@@ -106,14 +110,10 @@ static heat_status engine_upload(Engine* e) {
   e->h_op.clear();
   e->h_pw.clear();
   const int sms = sm_count();
-  long long total_nodes = 0;
-  for (heat_sim* s : e->sims) total_nodes += s->nn;
   long long item_base = 0;
   for (size_t i = 0; i < e->sims.size(); ++i) {
     SimDev d = e->sims[i]->dev;
-    // share of ~3 waves of 2 resident tiles per SM, by node count
-    const long long want = std::max(1LL, (long long)(6.0 * sms * (double)d.nn / (double)total_nodes));
-    tile_geometry(d, e->ks, want);
+    tile_geometry(d, e->ks);
     d.partial = e->d_partial + 4 * item_base;
     item_base += std::max(d.ntiles, d.npw);
     for (int t = 0; t < d.ntiles; ++t) e->h_op.push_back(make_int2((int)i, t));
@@ -152,14 +152,30 @@ static heat_status engine_capture(Engine* e) {
   // the instantiated graph is then launched on the engine's stream.
   cudaStream_t cap;
   CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  // Each kernel may launch while its predecessor finishes (programmatic
+  // dependent launch); the kernels wait for the predecessor's results with
+  // cudaGridDependencySynchronize after their static prologue.
+  auto launch = [&](TileFn fn, int grid, int block, const int2* work, const int* nwork) -> cudaError_t {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = cap;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, (const SimDev*)e->d_sims, work, nwork);
+  };
   cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
-    e->ks.open<<<e->grid_op, e->ks.open_threads, 0, cap>>>(e->d_sims, e->d_work_op, e->d_nwork);
-    for (int it = 0; it < e->iters_per_tick; ++it) {
-      e->ks.apply<<<e->grid_op, e->ks.apply_threads, 0, cap>>>(e->d_sims, e->d_work_op, e->d_nwork);
-      e->ks.update<<<e->grid_pw, kPwThreads, 0, cap>>>(e->d_sims, e->d_work_pw, e->d_nwork + 1);
+    cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork);
+    for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
+      lerr = launch(e->ks.apply, e->grid_op, e->ks.apply_threads, e->d_work_op, e->d_nwork);
+      if (lerr == cudaSuccess) lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1);
     }
     err = cudaStreamEndCapture(cap, &e->graph);
+    if (err == cudaSuccess && lerr != cudaSuccess) err = lerr;
   }
   cudaStreamDestroy(cap);
   if (err != cudaSuccess) {
@@ -243,9 +259,11 @@ void engine_destroy(Engine* e) {
 }
 
 heat_status engine_refresh(Engine* e) {
+  const int g_op = e->grid_op, g_pw = e->grid_pw;
   heat_status st = engine_upload(e);
   if (st != HEAT_OK) return st;
-  return engine_capture(e);  // grids may have changed
+  if (!e->gexec || e->grid_op != g_op || e->grid_pw != g_pw) return engine_capture(e);
+  return HEAT_OK;
 }
 
 heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters) {

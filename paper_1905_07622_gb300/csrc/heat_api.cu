@@ -459,6 +459,60 @@ extern "C" heat_status heat_step(heat_sim* s, int nsteps, heat_step_stats* stats
   return engine_step_all(s->eng, nsteps, stats ? stats : nullptr, 1);
 }
 
+// ------------------------------------------------------------------ batches
+
+struct heat_batch {
+  std::vector<heat_sim*> sims;
+  heat::Engine* eng = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+extern "C" heat_status heat_batch_create(heat_sim* const* sims, int nsims, void* cuda_stream, heat_batch** out) {
+  if (!out) return set_error(HEAT_ERR_ARG, "heat_batch_create: out is NULL");
+  *out = nullptr;
+  if (!sims || nsims < 1) return set_error(HEAT_ERR_ARG, "heat_batch_create: need at least one simulation");
+  for (int i = 0; i < nsims; ++i) {
+    if (!sims[i]) return set_error(HEAT_ERR_ARG, "heat_batch_create: simulation %d is NULL", i);
+    if (sims[i]->prm.precision != sims[0]->prm.precision)
+      return set_error(HEAT_ERR_ARG, "heat_batch_create: simulation %d has a different precision", i);
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return set_error(HEAT_ERR_ARG, "heat_batch_create: simulation %d repeated", i);
+  }
+  heat_batch* b = new heat_batch();
+  b->sims.assign(sims, sims + nsims);
+  b->stream = (cudaStream_t)cuda_stream;
+  heat_status st = engine_create(b->sims.data(), nsims, sims[0]->prm.precision, b->stream, &b->eng);
+  if (st != HEAT_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return HEAT_OK;
+}
+
+extern "C" heat_status heat_batch_step(heat_batch* b, int nsteps, heat_step_stats* stats) {
+  if (!b) return set_error(HEAT_ERR_ARG, "heat_batch_step: batch is NULL");
+  if (nsteps < 0) return set_error(HEAT_ERR_ARG, "heat_batch_step: nsteps must be >= 0");
+  if (stats) std::memset(stats, 0, sizeof(heat_step_stats) * b->sims.size());
+  if (nsteps == 0) return HEAT_OK;
+  for (heat_sim* s : b->sims) {
+    if (s->prm.precision != b->sims[0]->prm.precision)
+      return set_error(HEAT_ERR_ARG, "heat_batch_step: a member's precision changed");
+    heat_status st = ensure_log(s, nsteps);
+    if (st != HEAT_OK) return st;
+  }
+  // members' parameters or logs may have changed since the last call
+  heat_status st = engine_refresh(b->eng);
+  if (st != HEAT_OK) return st;
+  return engine_step_all(b->eng, nsteps, stats, 1);
+}
+
+extern "C" void heat_destroy_batch(heat_batch* b) {
+  if (!b) return;
+  engine_destroy(b->eng);
+  delete b;
+}
+
 extern "C" heat_status heat_solve_transient(heat_sim* s, int nsteps, double* u_out, heat_step_stats* stats) {
   heat_status st = heat_step(s, nsteps, stats);
   if (st != HEAT_OK) return st;

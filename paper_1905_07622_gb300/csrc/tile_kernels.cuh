@@ -60,7 +60,14 @@ struct ItemCache {
 // Makes `cache` hold simulation `sim` (cur is the caller's register copy of
 // the cached id; every thread tracks the same sequence, so the branch is
 // uniform). Contains barriers when it reloads.
-__device__ __forceinline__ void cache_sim(const SimDev* __restrict__ sims, int sim, ItemCache& cache, int& cur) {
+//
+// The kernels are launched with programmatic dependent launch: a kernel may
+// start while the previous one is finishing. The descriptor is static (set at
+// upload), so it is copied before waiting; the scalars and vectors are the
+// previous kernel's results, so everything after cudaGridDependencySynchronize
+// (which returns at once when there is no programmatic predecessor).
+__device__ __forceinline__ void cache_sim(const SimDev* __restrict__ sims, int sim, ItemCache& cache, int& cur,
+                                          bool& dep_ready) {
   if (sim == cur) return;
   __syncthreads();  // the previous simulation's users are done
   if (threadIdx.x < 32) {
@@ -68,11 +75,19 @@ __device__ __forceinline__ void cache_sim(const SimDev* __restrict__ sims, int s
     uint4* dst = reinterpret_cast<uint4*>(&cache.s);
     for (int t = threadIdx.x; t < (int)(sizeof(SimDev) / sizeof(uint4)); t += 32) dst[t] = src[t];
     __syncwarp();
-    if (threadIdx.x == 0) cache.c = load_ctl(cache.s.sc);
   }
+  if (!dep_ready) {
+    cudaGridDependencySynchronize();
+    dep_ready = true;
+  }
+  if (threadIdx.x == 0) cache.c = load_ctl(cache.s.sc);
   __syncthreads();
   cur = sim;
 }
+
+// Lets the next kernel of the stream be launched (it still waits for this
+// one's completion before reading its results).
+__device__ __forceinline__ void allow_next_launch() { cudaTriggerProgrammaticLaunchCompletion(); }
 
 // Block sum of per-thread partials of type T: each warp sums in T, the warp
 // sums are converted to FP64 and added by thread 0 in warp order. (On this
@@ -197,10 +212,12 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
   __shared__ double red[3 * 32];
   __shared__ ItemCache cache;
   int cur = -1;
+  bool dep = false;
+  allow_next_launch();
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    cache_sim(sims, wi.x, cache, cur);
+    cache_sim(sims, wi.x, cache, cur, dep);
     const SimDev& s = cache.s;
     const Ctl& c = cache.c;
     const int phase = c.phase;
@@ -384,10 +401,12 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
   __shared__ double red[32];
   __shared__ ItemCache cache;
   int cur = -1;
+  bool dep = false;
+  allow_next_launch();
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    cache_sim(sims, wi.x, cache, cur);
+    cache_sim(sims, wi.x, cache, cur, dep);
     const SimDev& s = cache.s;
     const Ctl& c = cache.c;
     if (c.phase != PH_ITER) continue;
@@ -465,10 +484,12 @@ __global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict_
   __shared__ double red[32];
   __shared__ ItemCache cache;
   int cur = -1;
+  bool dep = false;
+  allow_next_launch();
   const int nwork = *nwork_p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
-    cache_sim(sims, wi.x, cache, cur);
+    cache_sim(sims, wi.x, cache, cur, dep);
     const SimDev& s = cache.s;
     const Ctl& c = cache.c;
     if (c.phase != PH_ITER) continue;

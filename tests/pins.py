@@ -210,3 +210,12 @@ def check_pcg_finite_termination() -> float:
     if delta > 1e-24 * delta_b:
         return np.inf
     return it / S.A_ff.shape[0]
+
+
+def oracle_steps(p, tight_rtol: float = 1e-13, direct_limit: int = 20000):
+    """Oracle step solutions for parity tests: sparse LU on small meshes, the
+    oracle's Algorithm 1 PCG at a tight tolerance on larger ones (the LU
+    fill-in of a 3-D 27-point stencil makes it slow beyond ~20K nodes)."""
+    if p.n_nodes <= direct_limit:
+        return transient.run(p, solver="direct")
+    return transient.run(p, solver="pcg", rtol=tight_rtol)

@@ -164,6 +164,57 @@ heat_status heat_batch_create(heat_sim* const* sims, int nsims, void* cuda_strea
 heat_status heat_batch_step(heat_batch* batch, int nsteps, heat_step_stats* stats);
 void heat_destroy_batch(heat_batch* batch);
 
+/* ---- serving --------------------------------------------------------------
+ * A request loop for transient simulations that arrive over time (the
+ * inverse problem's stream of forward solves, §5.3). A worker thread owns the
+ * GPU: it admits pending requests in arrival order while their device
+ * footprint fits the HBM budget and a slot is free (first fit: a request that
+ * does not fit does not block smaller ones behind it), keeps each admitted
+ * simulation resident until its last step, and advances all admitted
+ * simulations together in every kernel launch (continuous batching:
+ * simulations join and leave between ticks, at any point of the others'
+ * solves). A simulation's results do not depend on what it shares the GPU
+ * with: they are bitwise identical to heat_step on the same inputs. */
+typedef struct {
+  int nx, ny, nz;            /* mesh, as heat_create_mesh */
+  double origin[3], extent[3];
+  const double* rho_c;       /* host, Ne values (copied by heat_submit) */
+  const double* k;           /* host, Ne values (copied by heat_submit) */
+  const double* u0;          /* host, N values, or NULL for zero (copied) */
+  heat_bc bc;
+  heat_params params;
+  int nsteps;                /* time steps to run, >= 1 */
+} heat_request;
+
+typedef struct {
+  long long submitted, completed, failed;
+  int active, pending;
+  size_t hbm_in_use, hbm_budget;  /* bytes of admitted simulations / budget */
+  long long kernel_launches;      /* kernels launched by the worker */
+  double dof_cg_iters;            /* sum over completed requests of N * CG iterations */
+} heat_server_stats;
+
+/* hbm_budget_bytes: device memory the admitted simulations may hold in total;
+ * max_active >= 1: simulations admitted at once; cuda_stream: the worker's
+ * stream (NULL: the worker creates a non-blocking one). The calling thread's
+ * current device is used. */
+heat_status heat_server_create(size_t hbm_budget_bytes, int max_active, void* cuda_stream,
+                               heat_server** out);
+/* Queue a request (inputs are copied; NaN/Inf or non-positive coefficients
+ * and requests larger than the whole budget are rejected here). */
+heat_status heat_submit(heat_server* srv, const heat_request* req, uint64_t* ticket);
+/* *done = 1 once the request finished (successfully or not). */
+heat_status heat_poll(heat_server* srv, uint64_t ticket, int* done);
+/* Wait up to timeout_s seconds (HEAT_ERR_TIMEOUT after that) for a request;
+ * then copy its final state (N values, host; may be NULL), statistics and
+ * latency (submit to completion, seconds; may be NULL) and forget the
+ * ticket. Returns the request's own status. */
+heat_status heat_wait(heat_server* srv, uint64_t ticket, double timeout_s, double* u_out,
+                      heat_step_stats* stats, double* latency_s);
+heat_status heat_server_get_stats(heat_server* srv, heat_server_stats* out);
+/* Stops the worker; requests not yet finished are abandoned. */
+void heat_destroy_server(heat_server* srv);
+
 /* ---- operator-level entry points (device pointers, sim stream) ---------- */
 
 /* y = A' x with A = M/dt + theta K (§3.2: A = M + theta dt K scaled by 1/dt),

@@ -58,6 +58,23 @@ class heat_step_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class heat_request(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("origin", C.c_double * 3), ("extent", C.c_double * 3),
+                ("rho_c", C.c_void_p), ("k", C.c_void_p), ("u0", C.c_void_p),
+                ("bc", heat_bc), ("params", heat_params), ("nsteps", C.c_int)]
+
+
+class heat_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("active", C.c_int), ("pending", C.c_int), ("hbm_in_use", C.c_size_t),
+                ("hbm_budget", C.c_size_t), ("kernel_launches", C.c_longlong),
+                ("dof_cg_iters", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 # (name, restype, argtypes); heat_status functions return c_int
@@ -83,6 +100,12 @@ _SIGS = [
     ("heat_diagonal", C.c_int, [_VP, _VP]),
     ("heat_rhs", C.c_int, [_VP, C.c_int, _VP, _VP]),
     ("heat_flux_vector", C.c_int, [_VP, _VP]),
+    ("heat_server_create", C.c_int, [C.c_size_t, C.c_int, _VP, C.POINTER(_VP)]),
+    ("heat_submit", C.c_int, [_VP, C.POINTER(heat_request), C.POINTER(C.c_uint64)]),
+    ("heat_poll", C.c_int, [_VP, C.c_uint64, C.POINTER(C.c_int)]),
+    ("heat_wait", C.c_int, [_VP, C.c_uint64, C.c_double, _VP, C.POINTER(heat_step_stats), _DP]),
+    ("heat_server_get_stats", C.c_int, [_VP, C.POINTER(heat_server_stats)]),
+    ("heat_destroy_server", None, [_VP]),
     ("heat_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, _VP, C.POINTER(_VP)]),
     ("heat_batch_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
     ("heat_destroy_batch", None, [_VP]),
@@ -293,6 +316,68 @@ def heat_profile_iteration(sim, reps: int, flush=None):
     fb = flush.numel() * flush.element_size() if flush is not None else 0
     _check(_lib.heat_profile_iteration(sim, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba), C.byref(bu)))
     return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_server_create(hbm_budget_bytes: int, max_active: int, stream=None):
+    load_library()
+    out = C.c_void_p()
+    st = C.c_void_p(int(stream) if stream else 0)
+    _check(_lib.heat_server_create(int(hbm_budget_bytes), int(max_active), st, C.byref(out)))
+    return out
+
+
+def make_request(p, precision="fp32_refined", **param_overrides):
+    """heat_request for a workloads.Problem-like object; keep the returned
+    arrays alive until heat_submit returns (it copies them)."""
+    rc = np.ascontiguousarray(p.rho_c, dtype=np.float64)
+    kk = np.ascontiguousarray(p.k, dtype=np.float64)
+    u0 = np.ascontiguousarray(p.u0, dtype=np.float64) if p.u0 is not None else None
+    req = heat_request()
+    req.nx, req.ny, req.nz = p.nx, p.ny, p.nz
+    req.origin = (C.c_double * 3)(*p.origin)
+    req.extent = (C.c_double * 3)(*p.extent)
+    req.rho_c = rc.ctypes.data
+    req.k = kk.ctypes.data
+    req.u0 = u0.ctypes.data if u0 is not None else None
+    req.bc = make_bc(p.dirichlet, p.flux, p.flux_steps)
+    kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision)
+    kw.update(param_overrides)
+    req.params = heat_params_default(**kw)
+    req.nsteps = int(p.nsteps)
+    return req, (rc, kk, u0)
+
+
+def heat_submit(server, req) -> int:
+    t = C.c_uint64()
+    _check(_lib.heat_submit(server, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def heat_poll(server, ticket: int) -> bool:
+    d = C.c_int()
+    _check(_lib.heat_poll(server, C.c_uint64(ticket), C.byref(d)))
+    return bool(d.value)
+
+
+def heat_wait(server, ticket: int, n_nodes: int, timeout_s: float = 600.0):
+    """(u, stats, latency_s); raises HeatError on failure or timeout."""
+    u = np.empty(n_nodes, dtype=np.float64)
+    st = heat_step_stats()
+    lat = C.c_double()
+    _check(_lib.heat_wait(server, C.c_uint64(ticket), float(timeout_s), C.c_void_p(u.ctypes.data), C.byref(st),
+                          C.byref(lat)))
+    return u, st.as_dict(), lat.value
+
+
+def heat_server_get_stats(server) -> dict:
+    s = heat_server_stats()
+    _check(_lib.heat_server_get_stats(server, C.byref(s)))
+    return s.as_dict()
+
+
+def heat_destroy_server(server):
+    if server:
+        _lib.heat_destroy_server(server)
 
 
 def heat_batch_create(sims, stream=None):

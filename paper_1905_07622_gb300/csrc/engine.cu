@@ -73,6 +73,9 @@ struct Engine {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long launches = 0;  // kernels launched by the last engine_step_all
+  int* d_phases = nullptr;
+  int* h_phases = nullptr;
+  int phases_cap = 0;
   std::vector<SimDev> h_sims;
   std::vector<int2> h_op, h_pw;
 };
@@ -255,6 +258,8 @@ void engine_destroy(Engine* e) {
   cudaFree(e->d_unfinished);
   cudaFree(e->d_partial);
   if (e->h_unfinished) cudaFreeHost(e->h_unfinished);
+  if (e->d_phases) cudaFree(e->d_phases);
+  if (e->h_phases) cudaFreeHost(e->h_phases);
   delete e;
 }
 
@@ -332,6 +337,48 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
     }
   }
   return first_bad;
+}
+
+__global__ void k_gather_phases(const SimDev* __restrict__ sims, int nsims, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsims; i += gridDim.x * blockDim.x)
+    out[i] = *(volatile const int*)&sims[i].sc->phase;
+}
+
+heat_status engine_launch_ticks(Engine* e, int nticks) {
+  for (int t = 0; t < nticks; ++t) CUDA_TRY(cudaGraphLaunch(e->gexec, e->stream));
+  e->launches += (long long)nticks * (1 + 2 * e->iters_per_tick);
+  return HEAT_OK;
+}
+
+heat_status engine_read_phases(Engine* e, int* phases) {
+  const int n = (int)e->sims.size();
+  int* d = nullptr;
+  if (!e->d_phases || e->phases_cap < n) {  // grown on first use
+    if (e->d_phases) cudaFree(e->d_phases);
+    if (e->h_phases) cudaFreeHost(e->h_phases);
+    e->d_phases = nullptr;
+    e->h_phases = nullptr;
+    CUDA_TRY(cudaMalloc(&e->d_phases, sizeof(int) * n));
+    CUDA_TRY(cudaMallocHost(&e->h_phases, sizeof(int) * n));
+    e->phases_cap = n;
+  }
+  d = e->d_phases;
+  k_gather_phases<<<(n + 255) / 256, 256, 0, e->stream>>>(e->d_sims, n, d);
+  CUDA_TRY(cudaGetLastError());
+  e->launches += 1;
+  CUDA_TRY(cudaMemcpyAsync(e->h_phases, d, sizeof(int) * n, cudaMemcpyDeviceToHost, e->stream));
+  CUDA_TRY(cudaStreamSynchronize(e->stream));
+  std::memcpy(phases, e->h_phases, sizeof(int) * n);
+  return HEAT_OK;
+}
+
+long long engine_launches(const Engine* e) { return e->launches; }
+
+size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) {
+  const long long cols = (long long)((nx + 15 - 1) / 15 + 1) * ((ny + 15 - 1) / 15 + 1);  // 16x16 tiles, rounded up
+  const long long op = cols * (nz + 1);
+  const long long pw = (nn + kPwChunk - 1) / kPwChunk;
+  return (size_t)(sizeof(int2) * (op + pw) + sizeof(double) * 4 * std::max(op, pw) + sizeof(SimDev) + 64);
 }
 
 // Reads a buffer larger than L2 so the next kernel starts cold. Reading (not

@@ -45,6 +45,12 @@ heat_status sim_alloc(heat_sim* s, void** p, size_t bytes);
 heat_status sim_upload_desc(heat_sim* s);
 heat_status sim_read_scalars(heat_sim* s);
 heat_status sim_write_scalars(heat_sim* s);
+// Queue nsteps steps on a simulation (target, phase, counters; log capacity).
+heat_status sim_prepare_steps(heat_sim* s, int nsteps);
+// Device bytes a simulation of this size holds.
+size_t sim_footprint(long long nn, long long ne);
+// Statistics from the host copy of the scalars (after sim_read_scalars).
+void sim_stats(const heat_sim* s, heat_step_stats* o);
 
 // A set of simulations driven together by one captured tick graph.
 heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out);
@@ -54,6 +60,14 @@ heat_status engine_refresh(Engine* e);
 // Advance every sim of the engine by nsteps steps; stats[i] per sim (may be
 // NULL). reset_counters clears the per-call counters first.
 heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters);
+// Launch nticks ticks without waiting (the server drives its own loop).
+heat_status engine_launch_ticks(Engine* e, int nticks);
+// Phase of every simulation of the engine (host array of nsims ints); waits.
+heat_status engine_read_phases(Engine* e, int* phases);
+// Kernels launched so far by engine_launch_ticks / engine_step_all.
+long long engine_launches(const Engine* e);
+// Device bytes the engine needs for these simulations (work lists, partials).
+size_t engine_footprint(long long nn, long long nx, long long ny, long long nz);
 // Time reps CG iterations of the engine's first simulation (see heat_profile_iteration).
 heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
                            double* ms_update, double* bytes_apply, double* bytes_update);

@@ -445,6 +445,40 @@ static heat_status ensure_log(heat_sim* s, int nsteps) {
   return HEAT_OK;
 }
 
+heat_status heat::sim_prepare_steps(heat_sim* s, int nsteps) {
+  heat_status st = ensure_log(s, nsteps);
+  if (st != HEAT_OK) return st;
+  st = sim_read_scalars(s);
+  if (st != HEAT_OK) return st;
+  SimScalars* sc = s->h_sc;
+  sc->target = sc->step + nsteps;
+  sc->phase = PH_OPEN;
+  sc->status = ST_OK;
+  sc->count = 0;
+  sc->iters_total = 0;
+  sc->outer_total = 0;
+  sc->steps_total = 0;
+  sc->max_iters_step = 0;
+  return sim_write_scalars(s);
+}
+
+size_t heat::sim_footprint(long long nn, long long ne) {
+  // 12 FP64 and 6 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
+  return (size_t)nn * (12 * 8 + 6 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
+         4096 * sizeof(int) + 1024;
+}
+
+void heat::sim_stats(const heat_sim* s, heat_step_stats* o) {
+  const SimScalars* sc = s->h_sc;
+  o->steps = (int)sc->steps_total;
+  o->status = sc->phase == PH_FAILED ? sc->status : HEAT_OK;
+  o->iters = sc->iters_total;
+  o->outer = sc->outer_total;
+  o->max_iters_step = sc->max_iters_step;
+  o->last_rel_residual = sc->rel_res;
+  o->kernel_launches = 0;
+}
+
 extern "C" heat_status heat_step(heat_sim* s, int nsteps, heat_step_stats* stats) {
   if (!s) return set_error(HEAT_ERR_ARG, "heat_step: sim is NULL");
   if (nsteps < 0) return set_error(HEAT_ERR_ARG, "heat_step: nsteps must be >= 0");

@@ -59,3 +59,14 @@ def test_host_side_argument_checks_without_gpu(lib):
     api.heat_destroy_mesh(m)
     p = api.heat_params_default()
     assert p.resid_period == 50 and p.theta == 0.5
+
+
+def test_server_create_fails_cleanly_without_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1905_07622_gb300.api as api
+
+    with pytest.raises(api.HeatError) as e:
+        api.heat_server_create(1 << 30, 4)
+    assert e.value.status == api.HEAT_ERR_CUDA

@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison solve")
     ap.add_argument("--profile-reps", type=int, default=120)
+    ap.add_argument("--batch-sims", type=int, default=256, help="batched workload: 40^3 samples (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=150)
+    ap.add_argument("--serve-requests", type=int, default=40, help="serving stream length (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -240,6 +245,84 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- batch / serving
+
+def run_batch(hg, torch, nsims: int, nsteps: int, stream):
+    """256 independent 40^3 samples with log-normal k (seeds 3000+s), FP32
+    refined, one engine: every launch carries all samples."""
+    import workloads as W
+    ps = [W.lognormal_cube(s, n=40, nsteps=nsteps) for s in range(nsims)]
+    sims = [hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream) for p in ps]
+    b = hg.heat_batch_create([s.sim for s in sims], stream.cuda_stream)
+    try:
+        rc, _ = hg.heat_batch_step(b, 2, nsims)  # warm-up steps (graph capture, caches)
+        for s, p in zip(sims, ps):
+            hg.heat_set_state(s.sim, p.u0, s.n_nodes)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc, stats = hg.heat_batch_step(b, nsteps, nsims)
+        e.record(stream)
+        e.synchronize()
+        sec = a.elapsed_time(e) / 1e3
+        if rc != 0:
+            raise RuntimeError(hg.heat_last_error())
+        its = sum(st["iters"] for st in stats)
+        dof = sims[0].n_nodes
+        # the batch's CG-iteration kernels timed alone (L2 flushed before each launch)
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        prof = hg.heat_batch_profile_iteration(b, 20, flush)
+        peak, _ = measured_peaks()
+        achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
+        return {"workload": f"{nsims} x lognormal_cube_40 (68,921 DOF each), {nsteps} steps, dt=2e-3, theta=0.5, rtol 1e-10, fp32_refined",
+                "seconds": sec, "sims_per_s": nsims / sec, "dof_cg_iters_per_s": dof * its / sec,
+                "cg_iterations_per_sim_step": its / (nsims * nsteps),
+                "kernel_launches": stats[0]["kernel_launches"],
+                "roofline": {"bound": "hbm", "kernel": "k_apply_dot<float>", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "ms_per_launch": prof["ms_apply"],
+                             "algorithmic_bytes_per_launch": prof["bytes_apply"],
+                             "update_kernel": {"ms_per_launch": prof["ms_update"],
+                                               "achieved": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9}}}
+    finally:
+        hg.heat_destroy_batch(b)
+        for s in sims:
+            s.close()
+
+
+def run_serving(hg, nreq: int, rate: float, budget_gb: float):
+    """Poisson arrivals of serving_request(r) (edge U{20..120}, two-phase k,
+    50..300 steps, rtol 1e-8, fp32_refined) at `rate` per second."""
+    import numpy as np
+    import workloads as W
+    arrivals = W.poisson_arrivals(nreq, rate=rate)
+    ps = [W.serving_request(r) for r in range(nreq)]
+    reqs = [hg.make_request(p) for p in ps]  # inputs prepared before the clock starts
+    srv = hg.heat_server_create(int(budget_gb * (1 << 30)), 64)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for (req, keep), ta in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(hg.heat_submit(srv, req))
+        lat, its_dof = [], 0.0
+        for t, p in zip(tickets, ps):
+            u, st, l = hg.heat_wait(srv, t, p.n_nodes, timeout_s=3600.0)
+            lat.append(l)
+            its_dof += p.n_nodes * st["iters"]
+        wall = time.perf_counter() - t0
+        sst = hg.heat_server_get_stats(srv)
+    finally:
+        hg.heat_destroy_server(srv)
+    lat = np.array(lat)
+    return {"workload": f"{nreq} requests, Poisson {rate}/s, cubic Q1 20^3..120^3, two-phase k 10:1 at phi U[0.1,0.5], 50..300 steps, dt=1e-3, rtol 1e-8, fp32_refined, HBM budget {budget_gb} GB",
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "sims_per_s": nreq / wall, "dof_cg_iters_per_s": its_dof / wall, "wall_s": wall,
+            "offered_dof": float(sum(p.n_nodes for p in ps)), "kernel_launches": sst["kernel_launches"]}
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
@@ -357,6 +440,12 @@ def main():
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
     traffic = ncu_traffic(kernel_key)
 
+    batched = serving = None
+    if rank == 0 and args.batch_sims > 0:
+        batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream)
+    if rank == 0 and args.serve_requests > 0:
+        serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -380,6 +469,8 @@ def main():
             "clocks": clocks,
             "fp64_path": fp64,
             "final_field_rel_err_vs_fp64_path": final_err,
+            "batched": batched,
+            "serving": serving,
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",

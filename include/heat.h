@@ -275,6 +275,12 @@ heat_status heat_apply_dot_noalloc(int nx, int ny, int nz, const double extent[3
 heat_status heat_profile_iteration(heat_sim* sim, int reps, void* flush, size_t flush_bytes,
                                    double* ms_apply, double* ms_update,
                                    double* bytes_apply, double* bytes_update);
+/* The same for every member of a batch at once (each launch carries all of
+ * them); needs a prior heat_batch_step and leaves the members' solver state
+ * undefined. */
+heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flush, size_t flush_bytes,
+                                         double* ms_apply, double* ms_update,
+                                         double* bytes_apply, double* bytes_update);
 
 const char* heat_last_error(void);
 const char* heat_status_string(heat_status s);

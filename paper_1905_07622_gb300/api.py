@@ -110,6 +110,7 @@ _SIGS = [
     ("heat_batch_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
     ("heat_destroy_batch", None, [_VP]),
     ("heat_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
+    ("heat_batch_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
     ("heat_apply_dot_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, _DP, C.c_double, C.c_double, C.c_uint32,
                                          _VP, _VP, _VP, _VP, _VP]),
     ("heat_last_error", C.c_char_p, []),
@@ -410,6 +411,16 @@ def heat_apply_dot_noalloc(nx, ny, nz, extent, dt, theta, dirichlet_faces, coef,
     _check(_lib.heat_apply_dot_noalloc(int(nx), int(ny), int(nz), ext, float(dt), float(theta),
                                        int(dirichlet_faces), C.c_void_p(_dev_ptr(coef)), C.c_void_p(_dev_ptr(x)),
                                        C.c_void_p(_dev_ptr(y)), C.c_void_p(_dev_ptr(xdoty)), s))
+
+
+def heat_batch_profile_iteration(batch, reps: int, flush=None):
+    """heat_profile_iteration over every member of a batch."""
+    ma, mu, ba, bu = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    fp = C.c_void_p(_dev_ptr(flush)) if flush is not None else C.c_void_p(0)
+    fb = flush.numel() * flush.element_size() if flush is not None else 0
+    _check(_lib.heat_batch_profile_iteration(batch, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba),
+                                             C.byref(bu)))
+    return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
 
 
 def heat_last_error() -> str:

@@ -394,7 +394,6 @@ __global__ void k_flush_read(const uint4* __restrict__ p, size_t n, unsigned int
 
 heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
                            double* ms_update, double* bytes_apply, double* bytes_update) {
-  heat_sim* s = e->sims[0];
   const int chunk = 40;  // below the inner-solve cap and the true-residual period
   cudaEvent_t ev[4 * chunk];
   for (int i = 0; i < 4 * chunk; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
@@ -402,18 +401,21 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   heat_status st = HEAT_OK;
   for (int done = 0; done < reps && st == HEAT_OK;) {
     const int c = std::min(reps - done, chunk);
-    st = sim_read_scalars(s);
-    if (st != HEAT_OK) break;
-    SimScalars* sc = s->h_sc;
-    sc->phase = PH_ITER;
-    sc->iter = 1;
-    sc->iter_step = 0;
-    sc->restart = 1;
-    sc->thresh = -1.0;
-    sc->thresh_in = -1.0;
-    sc->count = 0;
-    if (!(sc->delta > 0.0)) sc->delta = 1.0;
-    st = sim_write_scalars(s);
+    for (heat_sim* s : e->sims) {  // every member iterates, none converges
+      st = sim_read_scalars(s);
+      if (st != HEAT_OK) break;
+      SimScalars* sc = s->h_sc;
+      sc->phase = PH_ITER;
+      sc->iter = 1;
+      sc->iter_step = 0;
+      sc->restart = 1;
+      sc->thresh = -1.0;
+      sc->thresh_in = -1.0;
+      sc->count = 0;
+      if (!(sc->delta > 0.0)) sc->delta = 1.0;
+      st = sim_write_scalars(s);
+      if (st != HEAT_OK) break;
+    }
     if (st != HEAT_OK) break;
     for (int i = 0; i < c; ++i) {
       if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
@@ -436,9 +438,12 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
       ta += a;
       tu += u;
     }
-    st = sim_read_scalars(s);
-    if (st == HEAT_OK && s->h_sc->phase != PH_ITER)
-      st = set_error(HEAT_ERR_BREAKDOWN, "profile: the iteration left PH_ITER (status %d)", s->h_sc->status);
+    for (heat_sim* s : e->sims) {
+      if (st != HEAT_OK) break;
+      st = sim_read_scalars(s);
+      if (st == HEAT_OK && s->h_sc->phase != PH_ITER)
+        st = set_error(HEAT_ERR_BREAKDOWN, "profile: the iteration left PH_ITER (status %d)", s->h_sc->status);
+    }
     done += c;
   }
   for (int i = 0; i < 4 * chunk; ++i) cudaEventDestroy(ev[i]);

@@ -541,6 +541,14 @@ extern "C" heat_status heat_batch_step(heat_batch* b, int nsteps, heat_step_stat
   return engine_step_all(b->eng, nsteps, stats, 1);
 }
 
+extern "C" heat_status heat_batch_profile_iteration(heat_batch* b, int reps, void* flush, size_t flush_bytes,
+                                                    double* ms_apply, double* ms_update, double* bytes_apply,
+                                                    double* bytes_update) {
+  if (!b || reps < 1 || !ms_apply || !ms_update || !bytes_apply || !bytes_update)
+    return set_error(HEAT_ERR_ARG, "heat_batch_profile_iteration: bad argument");
+  return engine_profile(b->eng, reps, flush, flush_bytes, ms_apply, ms_update, bytes_apply, bytes_update);
+}
+
 extern "C" void heat_destroy_batch(heat_batch* b) {
   if (!b) return;
   engine_destroy(b->eng);

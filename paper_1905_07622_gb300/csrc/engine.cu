@@ -22,19 +22,32 @@ struct KernelSet {
   TileFn open, apply, update;
   int sx, sy;
   int open_threads, apply_threads;
+  // warp-segment apply (FP32 paths); when set it replaces `apply`
+  TileFn apply_w;
+  int wsx, wny, wwarps;
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
-  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY};
+  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0};
+}
+
+template <int P, int SX, int SY, int WSX, int WNY, int WW>
+static KernelSet make_set_w() {
+  KernelSet k = make_set<P, SX, SY>();
+  k.apply_w = k_apply_dot_w<float, WSX, WNY, WW>;
+  k.wsx = WSX;
+  k.wny = WNY;
+  k.wwarps = WW;
+  return k;
 }
 
 static KernelSet kernel_set(int prec) {
   switch (prec) {
     case P_FP64: return make_set<P_FP64, 16, 16>();
-    case P_FP32_REFINED: return make_set<P_FP32_REFINED, 16, 16>();
-    default: return make_set<P_FP32_PLAIN, 16, 16>();
+    case P_FP32_REFINED: return make_set_w<P_FP32_REFINED, 16, 16, 16, 4, 4>();
+    default: return make_set_w<P_FP32_PLAIN, 16, 16, 16, 4, 4>();
   }
 }
 
@@ -64,7 +77,11 @@ struct Engine {
   SimDev* d_sims = nullptr;
   int2* d_work_op = nullptr;
   int2* d_work_pw = nullptr;
-  int* d_nwork = nullptr;  // [0] operator items, [1] pointwise items
+  int2* d_work_aw = nullptr;  // warp-segment apply items
+  long long cap_aw = 0;
+  int grid_aw = 0;
+  std::vector<int2> h_aw;
+  int* d_nwork = nullptr;  // [0] operator tiles, [1] pointwise chunks, [2] warp-apply items
   int* d_unfinished = nullptr;
   int* h_unfinished = nullptr;
   double* d_partial = nullptr;
@@ -99,6 +116,19 @@ static void tile_geometry(SimDev& d, const KernelSet& ks) {
   d.ntz = (levels + d.tz_len - 1) / d.tz_len;
   d.ntiles = d.ntx * d.nty * d.ntz;
   d.npw = (int)((d.nn + kPwChunk - 1) / kPwChunk);
+  d.w_ntx = d.w_nty = d.w_ntz = d.w_tz = d.w_ntiles = d.w_items = 0;
+  if (ks.apply_w) {
+    // segment tiles of about kSegNodes nodes, at least 4 levels (2 extra levels per tile)
+    constexpr int kSegNodes = 512;
+    d.w_ntx = (d.nx + 1 + ks.wsx - 3) / (ks.wsx - 2);
+    d.w_nty = (d.ny + 1 + ks.wny - 1) / ks.wny;
+    const int tz0 = std::max(4, std::min(levels, kSegNodes / ((ks.wsx - 2) * ks.wny)));
+    d.w_ntz = (levels + tz0 - 1) / tz0;
+    d.w_tz = (levels + d.w_ntz - 1) / d.w_ntz;
+    d.w_ntiles = d.w_ntx * d.w_nty * d.w_ntz;
+    const int spc = ks.wwarps * (32 / ks.wsx);
+    d.w_items = (d.w_ntiles + spc - 1) / spc;
+  }
 }
 
 static int sm_count() {
@@ -112,34 +142,60 @@ static heat_status engine_upload(Engine* e) {
   e->h_sims.clear();
   e->h_op.clear();
   e->h_pw.clear();
+  e->h_aw.clear();
   const int sms = sm_count();
   long long item_base = 0;
   for (size_t i = 0; i < e->sims.size(); ++i) {
     SimDev d = e->sims[i]->dev;
     tile_geometry(d, e->ks);
     d.partial = e->d_partial + 4 * item_base;
-    item_base += std::max(d.ntiles, d.npw);
+    item_base += std::max(std::max(d.ntiles, d.npw), d.w_items);
     for (int t = 0; t < d.ntiles; ++t) e->h_op.push_back(make_int2((int)i, t));
     for (int t = 0; t < d.npw; ++t) e->h_pw.push_back(make_int2((int)i, t));
+    for (int t = 0; t < d.w_items; ++t) e->h_aw.push_back(make_int2((int)i, t));
     e->h_sims.push_back(d);
   }
-  if ((long long)e->h_op.size() > e->cap_op || (long long)e->h_pw.size() > e->cap_pw || item_base > e->cap_partial)
+  if ((long long)e->h_op.size() > e->cap_op || (long long)e->h_pw.size() > e->cap_pw ||
+      (long long)e->h_aw.size() > e->cap_aw || item_base > e->cap_partial)
     return set_error(HEAT_ERR_ARG, "engine: work lists exceed their capacity");
-  const int nwork[2] = {(int)e->h_op.size(), (int)e->h_pw.size()};
+  const int nwork[3] = {(int)e->h_op.size(), (int)e->h_pw.size(), (int)e->h_aw.size()};
   CUDA_TRY(cudaMemcpyAsync(e->d_sims, e->h_sims.data(), sizeof(SimDev) * e->h_sims.size(), cudaMemcpyHostToDevice,
                            e->stream));
   CUDA_TRY(cudaMemcpyAsync(e->d_work_op, e->h_op.data(), sizeof(int2) * e->h_op.size(), cudaMemcpyHostToDevice,
                            e->stream));
   CUDA_TRY(cudaMemcpyAsync(e->d_work_pw, e->h_pw.data(), sizeof(int2) * e->h_pw.size(), cudaMemcpyHostToDevice,
                            e->stream));
+  if (!e->h_aw.empty())
+    CUDA_TRY(cudaMemcpyAsync(e->d_work_aw, e->h_aw.data(), sizeof(int2) * e->h_aw.size(), cudaMemcpyHostToDevice,
+                             e->stream));
   CUDA_TRY(cudaMemcpyAsync(e->d_nwork, nwork, sizeof(nwork), cudaMemcpyHostToDevice, e->stream));
   CUDA_TRY(cudaStreamSynchronize(e->stream));
-  int occ_op = 1, occ_pw = 1;
+  int occ_op = 1, occ_pw = 1, occ_aw = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_op, e->ks.apply, e->ks.apply_threads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pw, e->ks.update, kPwThreads, 0);
+  if (e->ks.apply_w) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_aw, e->ks.apply_w, 32 * e->ks.wwarps, 0);
   e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
   e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
+  e->grid_aw = (int)std::max(1LL, std::min<long long>(nwork[2], (long long)sms * std::max(1, occ_aw)));
   return HEAT_OK;
+}
+
+// The apply kernel of an iteration and its launch shape / work list.
+static void apply_launch(const Engine* e, TileFn* fn, int* grid, int* threads, const int2** work,
+                         const int** nwork) {
+  if (e->ks.apply_w) {
+    *fn = e->ks.apply_w;
+    *grid = e->grid_aw;
+    *threads = 32 * e->ks.wwarps;
+    *work = e->d_work_aw;
+    *nwork = e->d_nwork + 2;
+  } else {
+    *fn = e->ks.apply;
+    *grid = e->grid_op;
+    *threads = e->ks.apply_threads;
+    *work = e->d_work_op;
+    *nwork = e->d_nwork;
+  }
 }
 
 static heat_status engine_capture(Engine* e) {
@@ -170,11 +226,16 @@ static heat_status engine_capture(Engine* e) {
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, (const SimDev*)e->d_sims, work, nwork);
   };
+  TileFn afn;
+  int agrid, athreads;
+  const int2* awork;
+  const int* anwork;
+  apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork);
   cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
     cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork);
     for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
-      lerr = launch(e->ks.apply, e->grid_op, e->ks.apply_threads, e->d_work_op, e->d_nwork);
+      lerr = launch(afn, agrid, athreads, awork, anwork);
       if (lerr == cudaSuccess) lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1);
     }
     err = cudaStreamEndCapture(cap, &e->graph);
@@ -197,23 +258,23 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   e->prec = precision;
   e->ks = kernel_set(precision);
   e->stream = stream;
-  // capacities: the largest tile count any geometry choice can give, and the chunks
-  long long cap_op = 0, cap_pw = 0, cap_partial = 0;
+  // capacities: the geometry is a function of each mesh, so compute it
+  long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_partial = 0;
   for (heat_sim* s : e->sims) {
-    const long long cols = (long long)((s->dev.nx + e->ks.sx - 1) / (e->ks.sx - 1)) *
-                           ((s->dev.ny + e->ks.sy - 1) / (e->ks.sy - 1));
-    const long long op = cols * (long long)(s->dev.nz + 1);
-    const long long pw = (s->nn + kPwChunk - 1) / kPwChunk;
-    cap_op += op;
-    cap_pw += pw;
-    cap_partial += std::max(op, pw);
+    SimDev d = s->dev;
+    tile_geometry(d, e->ks);
+    cap_op += d.ntiles;
+    cap_pw += d.npw;
+    cap_aw += d.w_items;
+    cap_partial += std::max(std::max(d.ntiles, d.npw), d.w_items);
   }
-  if (cap_op > (1LL << 30) || cap_pw > (1LL << 30)) {
+  if (cap_op > (1LL << 30) || cap_pw > (1LL << 30) || cap_aw > (1LL << 30)) {
     delete e;
     return set_error(HEAT_ERR_ARG, "engine: too many work items");
   }
   e->cap_op = cap_op;
   e->cap_pw = cap_pw;
+  e->cap_aw = cap_aw;
   e->cap_partial = cap_partial;
   heat_status st = HEAT_OK;
   auto fail = [&](heat_status s) {
@@ -223,7 +284,8 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   if (cudaMalloc(&e->d_sims, sizeof(SimDev) * nsims) != cudaSuccess ||
       cudaMalloc(&e->d_work_op, sizeof(int2) * cap_op) != cudaSuccess ||
       cudaMalloc(&e->d_work_pw, sizeof(int2) * cap_pw) != cudaSuccess ||
-      cudaMalloc(&e->d_nwork, sizeof(int) * 2) != cudaSuccess ||
+      cudaMalloc(&e->d_work_aw, sizeof(int2) * std::max(1LL, cap_aw)) != cudaSuccess ||
+      cudaMalloc(&e->d_nwork, sizeof(int) * 3) != cudaSuccess ||
       cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_partial, sizeof(double) * 4 * cap_partial) != cudaSuccess ||
       cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess) {
@@ -254,6 +316,7 @@ void engine_destroy(Engine* e) {
   cudaFree(e->d_sims);
   cudaFree(e->d_work_op);
   cudaFree(e->d_work_pw);
+  cudaFree(e->d_work_aw);
   cudaFree(e->d_nwork);
   cudaFree(e->d_unfinished);
   cudaFree(e->d_partial);
@@ -264,10 +327,10 @@ void engine_destroy(Engine* e) {
 }
 
 heat_status engine_refresh(Engine* e) {
-  const int g_op = e->grid_op, g_pw = e->grid_pw;
+  const int g_op = e->grid_op, g_pw = e->grid_pw, g_aw = e->grid_aw;
   heat_status st = engine_upload(e);
   if (st != HEAT_OK) return st;
-  if (!e->gexec || e->grid_op != g_op || e->grid_pw != g_pw) return engine_capture(e);
+  if (!e->gexec || e->grid_op != g_op || e->grid_pw != g_pw || e->grid_aw != g_aw) return engine_capture(e);
   return HEAT_OK;
 }
 
@@ -378,7 +441,9 @@ size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) 
   const long long cols = (long long)((nx + 15 - 1) / 15 + 1) * ((ny + 15 - 1) / 15 + 1);  // 16x16 tiles, rounded up
   const long long op = cols * (nz + 1);
   const long long pw = (nn + kPwChunk - 1) / kPwChunk;
-  return (size_t)(sizeof(int2) * (op + pw) + sizeof(double) * 4 * std::max(op, pw) + sizeof(SimDev) + 64);
+  const long long aw = (nn + 511) / 512 / 8 + 8;  // warp-apply items (8 segment tiles of ~512 nodes)
+  return (size_t)(sizeof(int2) * (op + pw + aw) + sizeof(double) * 4 * std::max(std::max(op, pw), aw) +
+                  sizeof(SimDev) + 64);
 }
 
 // Reads a buffer larger than L2 so the next kernel starts cold. Reading (not
@@ -420,7 +485,14 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
     for (int i = 0; i < c; ++i) {
       if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
       cudaEventRecord(ev[4 * i + 0], e->stream);
-      e->ks.apply<<<e->grid_op, e->ks.apply_threads, 0, e->stream>>>(e->d_sims, e->d_work_op, e->d_nwork);
+      {
+        TileFn afn;
+        int agrid, athreads;
+        const int2* awork;
+        const int* anwork;
+        apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork);
+        afn<<<agrid, athreads, 0, e->stream>>>(e->d_sims, awork, anwork);
+      }
       cudaEventRecord(ev[4 * i + 1], e->stream);
       if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
       cudaEventRecord(ev[4 * i + 2], e->stream);

@@ -21,6 +21,7 @@
 #pragma once
 
 #include "op.cuh"
+#include "op_warp.cuh"
 
 namespace heat {
 
@@ -437,6 +438,70 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
     const T accv[1] = {acc};
     double tot[1];
     if (finish_item<T, 1>(s, wi.y, s.ntiles, accv, tot, red)) {
+      SimScalars* sc = s.sc;
+      sc->count = 0;
+      const double dq = tot[0];
+      sc->dq = dq;
+      if (!isfinite(dq)) fail(sc, ST_NONFINITE);
+      else if (!(dq > 0.0)) fail(sc, ST_BREAKDOWN);
+      else {
+        sc->alpha = sc->delta / dq;
+        sc->id ^= 1;
+        sc->restart = 0;
+      }
+    }
+  }
+}
+
+// Warp-segment version of k_apply_dot (op_warp.cuh): a work item is a group
+// of SPC consecutive segment tiles of one simulation; the level loop has no
+// block barrier. Same results contract as k_apply_dot.
+template <class T, int SX, int NY, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_apply_dot_w(const SimDev* __restrict__ sims,
+                                                            const int2* __restrict__ work,
+                                                            const int* __restrict__ nwork_p) {
+  constexpr int SPC = WARPS * (32 / SX);  // segments per block
+  __shared__ double red[32];
+  __shared__ ItemCache cache;
+  int cur = -1;
+  bool dep = false;
+  allow_next_launch();
+  const int nwork = *nwork_p;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 wi = work[w];
+    cache_sim(sims, wi.x, cache, cur, dep);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    if (c.phase != PH_ITER) continue;
+    const Geo g(s);
+    const int tile = wi.y * SPC + (int)threadIdx.x / SX;
+    const bool active = tile < s.w_ntiles;
+    const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
+    const T* __restrict__ r = IterVecs<T>::r(s);
+    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+    const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
+    T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
+    T* __restrict__ q = IterVecs<T>::q(s);
+    const bool rs = c.restart != 0;
+    const T beta = rs ? T(0) : (T)c.beta;
+    T acc = T(0);
+    warp_tile_op<T, SX, NY>(
+        g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
+        (T)s.theta, true,
+        [&](int m, bool live) -> DirRaw<T> {
+          if (!live) return {T(0), T(0), T(0)};
+          return {pinv[m], r[m], rs ? T(0) : dold[m]};
+        },
+        [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; },
+        [&](int m, bool dir, T y, T v) {
+          const T qv = dir ? T(0) : y;
+          q[m] = qv;
+          dnew[m] = v;
+          acc += v * qv;
+        });
+    const T accv[1] = {acc};
+    double tot[1];
+    if (finish_item<T, 1>(s, wi.y, s.w_items, accv, tot, red)) {
       SimScalars* sc = s.sc;
       sc->count = 0;
       const double dq = tot[0];

@@ -25,12 +25,14 @@ struct KernelSet {
   // warp-segment apply (FP32 paths); when set it replaces `apply`
   TileFn apply_w;
   int wsx, wny, wwarps;
+  int pw_chunk;  // nodes per pointwise (k_update) work item
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
-  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0};
+  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0,
+          pw_chunk<T>()};
 }
 
 template <int P, int SX, int SY, int WSX, int WNY, int WW>
@@ -115,7 +117,7 @@ static void tile_geometry(SimDev& d, const KernelSet& ks) {
   d.tz_len = (levels + ntz - 1) / ntz;
   d.ntz = (levels + d.tz_len - 1) / d.tz_len;
   d.ntiles = d.ntx * d.nty * d.ntz;
-  d.npw = (int)((d.nn + kPwChunk - 1) / kPwChunk);
+  d.npw = (int)((d.nn + ks.pw_chunk - 1) / ks.pw_chunk);
   d.w_ntx = d.w_nty = d.w_ntz = d.w_tz = d.w_ntiles = d.w_items = 0;
   if (ks.apply_w) {
     // segment tiles of about kSegNodes nodes, at least 4 levels (2 extra levels per tile)
@@ -440,7 +442,7 @@ long long engine_launches(const Engine* e) { return e->launches; }
 size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) {
   const long long cols = (long long)((nx + 15 - 1) / 15 + 1) * ((ny + 15 - 1) / 15 + 1);  // 16x16 tiles, rounded up
   const long long op = cols * (nz + 1);
-  const long long pw = (nn + kPwChunk - 1) / kPwChunk;
+  const long long pw = (nn + 2047) / 2048;  // the smaller (FP64) chunk
   const long long aw = (nn + 511) / 512 / 8 + 8;  // warp-apply items (8 segment tiles of ~512 nodes)
   return (size_t)(sizeof(int2) * (op + pw + aw) + sizeof(double) * 4 * std::max(std::max(op, pw), aw) +
                   sizeof(SimDev) + 64);

@@ -59,7 +59,7 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   int nx, ny, nz;             // elements per dimension
   int ntx, nty, ntz, ntiles;  // operator tiles (x, y, z counts and total)
   int tz_len;                 // node levels per operator tile
-  int npw;                    // pointwise chunks (kPwChunk nodes each)
+  int npw;                    // pointwise work items (pw_chunk nodes each)
   // warp-segment tiles of the FP32 apply: (SX-2) x NY x w_tz nodes each
   int w_ntx, w_nty, w_ntz, w_tz, w_ntiles;
   int w_items;                // work items (groups of segment tiles per block)

@@ -136,11 +136,16 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
   // the columns this thread stages: its own, and for the tile's last x column
   // and last y row the columns one further on
   const Col c00(g, i, j), c10(g, i + 1, j), c01(g, i, j + 1), c11(g, i + 1, j + 1);
-  T lm[8], lk[8];
+  // G_q = Tp_q + A_q Fp_q + B_q F_q and Tn_q = B_q Fp_q + A_q F_q with
+  // A_q = lam_q + lam_{q+4}, B_q = lam_q - lam_{q+4} (the two z-Walsh
+  // indices of xy index q), linear in (rho_c, k) with these coefficients:
+  T am[4], ak[4], bm[4], bk[4];
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    lm[w] = sa * lam_m<T>(s, w);
-    lk[w] = sb * lam_k<T>(s, w);
+  for (int q = 0; q < 4; ++q) {
+    am[q] = sa * (lam_m<T>(s, q) + lam_m<T>(s, q + 4));
+    ak[q] = sb * (lam_k<T>(s, q) + lam_k<T>(s, q + 4));
+    bm[q] = sa * (lam_m<T>(s, q) - lam_m<T>(s, q + 4));
+    bk[q] = sb * (lam_k<T>(s, q) - lam_k<T>(s, q + 4));
   }
   const int estride = g.nx * g.ny;
   const int ebase = elem_col ? i + g.nx * j : 0;
@@ -231,11 +236,11 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
         T G[4], Tn[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const T lo = Fp[q] + Fc[q], hi = Fp[q] - Fc[q];   // forward z (wz = 0, 1)
-          const T y0 = (rc * lm[q] + kc * lk[q]) * lo;       // scale
-          const T y1 = (rc * lm[q + 4] + kc * lk[q + 4]) * hi;
-          G[q] = Tp[q] + (y0 + y1);                          // inverse z: bottom half
-          Tn[q] = y0 - y1;                                   // inverse z: top half
+          // forward z, scaling and inverse z in one: bottom half into the face
+          // sum, top half carried to the next level
+          const T A = rc * am[q] + kc * ak[q], B = rc * bm[q] + kc * bk[q];
+          G[q] = Tp[q] + A * Fp[q] + B * Fc[q];
+          Tn[q] = B * Fp[q] + A * Fc[q];
         }
         // inverse y on the finished face level L-1
         rj[0] = G[0] + G[2];

@@ -46,25 +46,30 @@ __device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, cons
   const int ebase = c + g.nx * (j0 - 1);  // element index of element row 0 at level 0
   const int estride = g.nx * g.ny, pxy = g.pxy, gnz = g.nz, px = g.px, enx = g.nx;
   const bool dz0 = (g.dir & 16u) != 0, dz1 = (g.dir & 32u) != 0;
-  T lm[8], lk[8];
+  // With lam_q and lam'_q = lam_{q+4} (the two z-Walsh indices of an xy index
+  // q), the face sum and the element's top half are
+  //   G_q = Tp_q + A_q Fp_q + B_q F_q,  Tn_q = B_q Fp_q + A_q F_q,
+  //   A_q = lam_q + lam'_q,  B_q = lam_q - lam'_q,
+  // and A_q, B_q are linear in (rho_c, k) with these coefficients:
+  T am[4], ak[4], bm[4], bk[4];
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    lm[w] = sa * lam_m<T>(s, w);
-    lk[w] = sb * lam_k<T>(s, w);
+  for (int q = 0; q < 4; ++q) {
+    am[q] = sa * (lam_m<T>(s, q) + lam_m<T>(s, q + 4));
+    ak[q] = sb * (lam_k<T>(s, q) + lam_k<T>(s, q + 4));
+    bm[q] = sa * (lam_m<T>(s, q) - lam_m<T>(s, q + 4));
+    bk[q] = sb * (lam_k<T>(s, q) - lam_k<T>(s, q + 4));
   }
   using Raw = decltype(fetch(0, false));
   using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
   Raw raw[NR];
   CoefT cf[NF];
+  const unsigned rstat = rin & ~(mask ? rdxy : 0u);  // rows that can be live at any level
   auto fetch_level = [&](int L) {
-    const bool kin = L >= 0 && L <= gnz;
-    const bool dk = mask && ((dz0 && L == 0) || (dz1 && L == gnz));
+    const bool lev = L >= 0 && L <= gnz && !(mask && ((dz0 && L == 0) || (dz1 && L == gnz)));
+    const unsigned lv = lev ? rstat : 0u;
     const int off = nbase + L * pxy;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const bool live = ((rin >> r) & 1u) && kin && !dk && !(mask && ((rdxy >> r) & 1u));
-      raw[r] = fetch(off + r * px, live);
-    }
+    for (int r = 0; r < NR; ++r) raw[r] = fetch(off + r * px, (lv >> r) & 1u);
   };
   auto fetch_coef = [&](int E) {
     const bool ek = E >= 0 && E < gnz;
@@ -119,11 +124,9 @@ __device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, cons
         const T rc = cf[r].x, kc = cf[r].y;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const T lo = Fp[r][q] + F[r][q], hi = Fp[r][q] - F[r][q];
-          const T y0 = (rc * lm[q] + kc * lk[q]) * lo;
-          const T y1 = (rc * lm[q + 4] + kc * lk[q + 4]) * hi;
-          G[r][q] = Tp[r][q] + (y0 + y1);
-          Tp[r][q] = y0 - y1;
+          const T A = rc * am[q] + kc * ak[q], B = rc * bm[q] + kc * bk[q];
+          G[r][q] = Tp[r][q] + A * Fp[r][q] + B * F[r][q];
+          Tp[r][q] = B * Fp[r][q] + A * F[r][q];
         }
       }
       if (t <= tzl) fetch_coef(L);

@@ -25,8 +25,11 @@
 
 namespace heat {
 
-constexpr int kPwChunk = 1024;    // nodes per pointwise work item
-constexpr int kPwThreads = 256;   // 4 nodes per thread
+constexpr int kPwThreads = 256;
+// Nodes per pointwise work item: 16 per thread in FP32, 8 in FP64 (four
+// resp. two float4/double2 groups of 4 nodes, all loaded before any is used).
+template <class T> __host__ __device__ constexpr int pw_quads() { return sizeof(T) == 4 ? 4 : 2; }
+template <class T> __host__ __device__ constexpr int pw_chunk() { return kPwThreads * 4 * pw_quads<T>(); }
 
 // Control scalars of a simulation (written only by earlier kernels, or by
 // the last block after all of the simulation's items of this kernel).
@@ -559,9 +562,10 @@ __global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict_
     const Ctl& c = cache.c;
     if (c.phase != PH_ITER) continue;
     const bool resid_it = (P == P_FP64) && s.resid_period > 0 && c.iter > 0 && (c.iter % s.resid_period) == 0;
+    constexpr int QPT = pw_quads<T>();
     const int nn = (int)s.nn;
-    const int base = wi.y * kPwChunk;
-    const int end = min(base + kPwChunk, nn);
+    const int base = wi.y * pw_chunk<T>();
+    const int end = min(base + pw_chunk<T>(), nn);
     T* __restrict__ x = (P == P_FP64) ? reinterpret_cast<T*>(s.vec64[c.ix]) : reinterpret_cast<T*>(s.e32);
     T* __restrict__ r = const_cast<T*>(IterVecs<T>::r(s));
     const T* __restrict__ pinv = IterVecs<T>::pinv(s);
@@ -570,34 +574,41 @@ __global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict_
     const T alpha = (T)c.alpha;
     const bool zero_x = (P != P_FP64) && c.iter == 0;  // the inner solve starts from e = 0
     T part[1] = {T(0)};  // per-thread partial in T, FP64 from the warp sums on
-    for (int n = base + 4 * (int)threadIdx.x; n < end; n += 4 * (int)blockDim.x) {
-      if (n + 3 < end) {
-        Quad<T> xv, dv, rv, qv, pv;
-        dv.load(d + n);
-        if (zero_x) {
+    // QPT groups of 4 nodes per thread, group u at base + 4*tid + u*4*blockDim
+    // (coalesced per group); every load is issued before any result is used
+    Quad<T> xv[QPT], dv[QPT], rv[QPT], qv[QPT], pv[QPT];
+    bool full[QPT];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) xv.v[a] = T(0);
-        } else {
-          xv.load(x + n);
-        }
+    for (int u = 0; u < QPT; ++u) {
+      const int n = base + 4 * ((int)threadIdx.x + u * (int)blockDim.x);
+      full[u] = n + 3 < end;
+      if (full[u]) {
+        dv[u].load(d + n);
+        if (!zero_x) xv[u].load(x + n);
         if (!resid_it) {
-          rv.load(r + n);
-          qv.load(q + n);
-          pv.load(pinv + n);
+          rv[u].load(r + n);
+          qv[u].load(q + n);
+          pv[u].load(pinv + n);
         }
+      }
+    }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) xv.v[a] += alpha * dv.v[a];
-        xv.store(x + n);
+    for (int u = 0; u < QPT; ++u) {
+      const int n = base + 4 * ((int)threadIdx.x + u * (int)blockDim.x);
+      if (full[u]) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv[u].v[a] = (zero_x ? T(0) : xv[u].v[a]) + alpha * dv[u].v[a];
+        xv[u].store(x + n);
         if (!resid_it) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            rv.v[a] -= alpha * qv.v[a];
-            part[0] += rv.v[a] * rv.v[a] * pv.v[a];
+            rv[u].v[a] -= alpha * qv[u].v[a];
+            part[0] += rv[u].v[a] * rv[u].v[a] * pv[u].v[a];
           }
-          rv.store(r + n);
+          rv[u].store(r + n);
         }
       } else {
-        for (int m = n; m < end; ++m) {
+        for (int m = n; m < end; ++m) {  // ragged end of the mesh
           x[m] = (zero_x ? T(0) : x[m]) + alpha * d[m];
           if (!resid_it) {
             const T rn = r[m] - alpha * q[m];

@@ -184,24 +184,33 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, x: float) -> float:
+def _all_reduce(world, x: float, op: str) -> float:
+    """Reduce a scalar over ranks (NCCL on GPUs, gloo on CPU processes)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(world, x: float) -> float:
+    return _all_reduce(world, x, "max")
 
 
 def sum_over_ranks(world, x: float) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _all_reduce(world, x, "sum")
+
+
+def aggregate(world, seconds: float, units: float):
+    """Whole-job throughput of replicas: every rank's units over the slowest
+    rank's time (the ranks run independent simulations; no data-path
+    collective)."""
+    t = max_over_ranks(world, seconds)
+    u = sum_over_ranks(world, units)
+    return u / t, t, u
 
 
 # ---------------------------------------------------------------- reference arm
@@ -408,11 +417,8 @@ def main():
     clocks = clk.summary()
     ms_e2e, its_e2e, _ = timed(forward_host, args.steps, 1)
 
-    T = max_over_ranks(world, sum(ms) / 1e3)
-    units = sum_over_ranks(world, float(nn) * its)
-    value = units / T
-    T2 = max_over_ranks(world, sum(ms_e2e) / 1e3)
-    value_e2e = sum_over_ranks(world, float(nn) * its_e2e) / T2
+    value, T, units = aggregate(world, sum(ms) / 1e3, float(nn) * its)
+    value_e2e, _, _ = aggregate(world, sum(ms_e2e) / 1e3, float(nn) * its_e2e)
 
     # accuracy of this configuration's final field vs the FP64 path (same GPU)
     u_ref = None

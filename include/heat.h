@@ -135,6 +135,18 @@ heat_status heat_set_state(heat_sim* sim, const double* u, int on_device);
 /* Copy the current temperature U^n (N values) out. */
 heat_status heat_get_state(heat_sim* sim, double* u, int on_device);
 
+/* Checkpoint / resume. heat_get_history copies U^n and U^{n-1} (N values
+ * each; u_prev2 may be NULL) and the number of completed steps n (used by the
+ * flux schedule); *have_prev = 0 when U^{n-1} is not defined (no step since the
+ * last heat_set_state). heat_set_history restores them (u_prev2 == NULL: no
+ * history): a simulation resumed this way continues bitwise identically to
+ * one that was never interrupted. Dirichlet nodes are overwritten with their
+ * values. */
+heat_status heat_get_history(heat_sim* sim, double* u_prev, double* u_prev2, int* step, int* have_prev,
+                             int on_device);
+heat_status heat_set_history(heat_sim* sim, const double* u_prev, const double* u_prev2, int step,
+                             int on_device);
+
 /* Advance nsteps time steps (Algorithm 1 per step, x0 = 2U^{n-1} - U^{n-2}).
  * stats may be NULL. Returns the first failing step's status, if any. */
 heat_status heat_step(heat_sim* sim, int nsteps, heat_step_stats* stats);

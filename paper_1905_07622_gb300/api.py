@@ -91,6 +91,8 @@ _SIGS = [
     ("heat_set_params", C.c_int, [_VP, C.POINTER(heat_params)]),
     ("heat_set_state", C.c_int, [_VP, _VP, C.c_int]),
     ("heat_get_state", C.c_int, [_VP, _VP, C.c_int]),
+    ("heat_get_history", C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    ("heat_set_history", C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int]),
     ("heat_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
     ("heat_solve_transient", C.c_int, [_VP, C.c_int, _VP, C.POINTER(heat_step_stats)]),
     ("heat_step_iterations", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
@@ -249,6 +251,24 @@ def heat_get_state(sim, n_nodes, out=None):
     u = np.empty(n_nodes, dtype=np.float64)
     _check(_lib.heat_get_state(sim, C.c_void_p(u.ctypes.data), 0))
     return u
+
+
+def heat_get_history(sim, n_nodes):
+    """Checkpoint: (U^n, U^{n-1} or None, completed steps) as host arrays."""
+    u1 = np.empty(n_nodes, dtype=np.float64)
+    u2 = np.empty(n_nodes, dtype=np.float64)
+    step, hp = C.c_int(), C.c_int()
+    _check(_lib.heat_get_history(sim, C.c_void_p(u1.ctypes.data), C.c_void_p(u2.ctypes.data), C.byref(step),
+                                 C.byref(hp), 0))
+    return u1, (u2 if hp.value else None), step.value
+
+
+def heat_set_history(sim, u_prev, u_prev2, step: int, n_nodes: int):
+    """Resume from heat_get_history's output."""
+    a = _host_f64(u_prev, n_nodes)
+    b = _host_f64(u_prev2, n_nodes) if u_prev2 is not None else None
+    _check(_lib.heat_set_history(sim, C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data if b is not None else 0),
+                                 int(step), 0))
 
 
 def heat_step(sim, nsteps: int) -> dict:

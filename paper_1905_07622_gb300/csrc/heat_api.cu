@@ -431,6 +431,46 @@ extern "C" heat_status heat_get_state(heat_sim* s, double* u, int on_device) {
   return HEAT_OK;
 }
 
+extern "C" heat_status heat_get_history(heat_sim* s, double* u_prev, double* u_prev2, int* step, int* have_prev,
+                                        int on_device) {
+  if (!s || !u_prev) return set_error(HEAT_ERR_ARG, "heat_get_history: null argument");
+  heat_status st = sim_read_scalars(s);
+  if (st != HEAT_OK) return st;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(u_prev, s->dev.vec64[s->h_sc->iu1], (size_t)s->nn * 8, kind, s->stream));
+  if (u_prev2 && s->h_sc->have_prev)
+    CUDA_TRY(cudaMemcpyAsync(u_prev2, s->dev.vec64[s->h_sc->iu2], (size_t)s->nn * 8, kind, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (step) *step = s->h_sc->step;
+  if (have_prev) *have_prev = s->h_sc->have_prev;
+  return HEAT_OK;
+}
+
+extern "C" heat_status heat_set_history(heat_sim* s, const double* u_prev, const double* u_prev2, int step,
+                                        int on_device) {
+  if (!s || !u_prev || step < 0) return set_error(HEAT_ERR_ARG, "heat_set_history: bad argument");
+  if (!on_device) {
+    for (long long n = 0; n < s->nn; ++n)
+      if (!std::isfinite(u_prev[n]) || (u_prev2 && !std::isfinite(u_prev2[n])))
+        return set_error(HEAT_ERR_NONFINITE, "heat_set_history: non-finite value at node %lld", n);
+  }
+  heat_status st = sim_read_scalars(s);
+  if (st != HEAT_OK) return st;
+  reset_scalars(s->h_sc);  // slots: U^{n-1} in vec64[0], U^{n-2} in vec64[1]
+  st = copy_in(s, s->dev.vec64[0], u_prev, (size_t)s->nn * 8, on_device);
+  if (st != HEAT_OK) return st;
+  k_impose_dirichlet<<<grid_for(s->nn, 256), 256, 0, s->stream>>>(s->d_dev, s->dev.vec64[0]);
+  if (u_prev2) {
+    st = copy_in(s, s->dev.vec64[1], u_prev2, (size_t)s->nn * 8, on_device);
+    if (st != HEAT_OK) return st;
+    k_impose_dirichlet<<<grid_for(s->nn, 256), 256, 0, s->stream>>>(s->d_dev, s->dev.vec64[1]);
+  }
+  CUDA_TRY(cudaGetLastError());
+  s->h_sc->have_prev = u_prev2 ? 1 : 0;
+  s->h_sc->step = step;
+  return sim_write_scalars(s);
+}
+
 static heat_status ensure_log(heat_sim* s, int nsteps) {
   if (nsteps <= s->iters_log_cap) return HEAT_OK;
   void* p;

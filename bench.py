@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=40, help="serving stream length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning table")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -257,11 +258,25 @@ def run_reference(args, world, rank):
 
 # ---------------------------------------------------------------- batch / serving
 
-def run_batch(hg, torch, nsims: int, nsteps: int, stream):
+def autotune(hg, p, precision, stream, flush, reps=20):
+    """Tune the kernel table for this problem's size bucket and precision
+    (untimed; one step first so the solver vectors hold a real iteration)."""
+    with hg.Simulation.from_problem(p, precision=precision, stream=stream.cuda_stream) as s:
+        s.step(1)
+        table, ms = hg.heat_autotune(s.sim, reps, flush)
+    return {"table": table, "best_ms_apply": ms}
+
+
+def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
     """256 independent 40^3 samples with log-normal k (seeds 3000+s), FP32
     refined, one engine: every launch carries all samples."""
     import workloads as W
     ps = [W.lognormal_cube(s, n=40, nsteps=nsteps) for s in range(nsims)]
+    tuning = None
+    if tune:
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        tuning = autotune(hg, W.lognormal_cube(0, n=40, nsteps=2), "fp32_refined", stream, flush)
+        del flush
     sims = [hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream) for p in ps]
     b = hg.heat_batch_create([s.sim for s in sims], stream.cuda_stream)
     try:
@@ -288,7 +303,7 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream):
         return {"workload": f"{nsims} x lognormal_cube_40 (68,921 DOF each), {nsteps} steps, dt=2e-3, theta=0.5, rtol 1e-10, fp32_refined",
                 "seconds": sec, "sims_per_s": nsims / sec, "dof_cg_iters_per_s": dof * its / sec,
                 "cg_iterations_per_sim_step": its / (nsims * nsteps),
-                "kernel_launches": stats[0]["kernel_launches"],
+                "kernel_launches": stats[0]["kernel_launches"], "tuning": tuning,
                 "roofline": {"bound": "hbm", "kernel": "k_apply_dot<float>", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak, "ms_per_launch": prof["ms_apply"],
                              "algorithmic_bytes_per_launch": prof["bytes_apply"],
@@ -365,15 +380,17 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.batch_only:  # the batched workload alone (used for profiling captures)
-        print(json.dumps({"batched": run_batch(hg, torch, args.batch_sims, args.batch_steps, stream)}), flush=True)
+        print(json.dumps({"batched": run_batch(hg, torch, args.batch_sims, args.batch_steps, stream,
+                                               not args.no_autotune)}), flush=True)
         return
     p = W.inclusions_cube(nsteps=args.nsteps)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream, flush)
     sim = hg.Simulation.from_problem(p, precision=args.precision, stream=stream.cuda_stream)
     nn, ne = sim.n_nodes, sim.n_elems
     rc_d = torch.tensor(p.rho_c, device="cuda")
     k_d = torch.tensor(p.k, device="cuda")
     u0_d = torch.tensor(p.u0, device="cuda")
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def forward_device():
         hg.heat_set_coeffs(sim.sim, rc_d, k_d, ne)
@@ -452,7 +469,7 @@ def main():
 
     batched = serving = None
     if rank == 0 and args.batch_sims > 0:
-        batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream)
+        batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 
@@ -466,7 +483,8 @@ def main():
             "config": {"workload": WORKLOAD, "precision": args.precision, "dof": nn,
                        "time_steps_per_forward_solve": args.nsteps, "cg_iterations_per_step_avg": its / (args.steps * args.nsteps),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "l2": "flushed between timed steps (256 MiB overwrite)"},
+                       "l2": "flushed between timed steps (256 MiB overwrite)",
+                       "kernel_tuning": tuning},
             "e2e": {"value": value_e2e, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (2 * ne + nn), "d2h_bytes_per_step": 8 * nn},
             "gpu_launches": launches,

@@ -294,6 +294,44 @@ heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flus
                                          double* ms_apply, double* ms_update,
                                          double* bytes_apply, double* bytes_update);
 
+/* ---- kernel tuning ------------------------------------------------------ */
+
+/* The process-wide table the kernel choice of every engine comes from; it is
+ * read when a simulation's engine (first heat_step after a change of
+ * precision), a batch or a server is built, and engines built earlier keep
+ * their kernels. The choice depends on the precision and on each mesh's own
+ * node count only, so a simulation gives bitwise the same results alone and in
+ * any batch built under the same table.
+ *   variant[p]: for heat_precision p, the warp-segment apply kernel variant
+ *     (0 .. heat_tuning_num_variants()-1) or -1 for the block-tile apply.
+ *     Default {-1, 0, 0}.
+ *   seg_nodes[b]: output nodes per warp-segment tile for meshes of bucket b
+ *     (N < 200000, N < 4000000, larger); 32 .. 2^20, default 512. */
+typedef struct heat_tuning {
+  int variant[3];
+  int seg_nodes[3];
+} heat_tuning;
+int heat_tuning_num_variants(void);
+/* Shape of variant v: segment width in nodes along x (one lane per node),
+ * element rows along y per lane, warps per block, and whether an FP64 kernel
+ * exists. HEAT_ERR_ARG for an unknown v. */
+heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64);
+heat_status heat_tuning_get(heat_tuning* t);
+/* HEAT_ERR_ARG (table unchanged) for an unknown variant, a variant without
+ * an FP64 kernel in variant[HEAT_FP64], or a segment size out of range. */
+heat_status heat_tuning_set(const heat_tuning* t);
+/* Time the apply kernel of one CG iteration (as heat_profile_iteration, `reps`
+ * launches after 3 warm-up launches, flush as there) for every candidate
+ * (block tile; each variant with a segment size of 256, 512, 1024 or 2048
+ * nodes) on this simulation's mesh and precision, and store the fastest in
+ * the table entries of that precision and of the mesh's size bucket. Outputs
+ * the resulting table and the winner's mean ms per launch (either may be
+ * NULL). Needs a prior heat_step; leaves the simulation's solver state
+ * undefined (call heat_set_state or heat_set_history before stepping again);
+ * its next heat_step builds its engine under the new table. */
+heat_status heat_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, heat_tuning* best,
+                          double* best_ms);
+
 const char* heat_last_error(void);
 const char* heat_status_string(heat_status s);
 

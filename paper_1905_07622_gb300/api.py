@@ -65,6 +65,13 @@ class heat_request(C.Structure):
                 ("bc", heat_bc), ("params", heat_params), ("nsteps", C.c_int)]
 
 
+class heat_tuning(C.Structure):
+    _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3)]
+
+    def as_dict(self):
+        return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes)}
+
+
 class heat_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
                 ("active", C.c_int), ("pending", C.c_int), ("hbm_in_use", C.c_size_t),
@@ -115,6 +122,12 @@ _SIGS = [
     ("heat_batch_profile_iteration", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, _DP, _DP, _DP, _DP]),
     ("heat_apply_dot_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, _DP, C.c_double, C.c_double, C.c_uint32,
                                          _VP, _VP, _VP, _VP, _VP]),
+    ("heat_tuning_num_variants", C.c_int, []),
+    ("heat_tuning_variant", C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+    ("heat_tuning_get", C.c_int, [C.POINTER(heat_tuning)]),
+    ("heat_tuning_set", C.c_int, [C.POINTER(heat_tuning)]),
+    ("heat_autotune", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, C.POINTER(heat_tuning), _DP]),
     ("heat_last_error", C.c_char_p, []),
     ("heat_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -441,6 +454,41 @@ def heat_batch_profile_iteration(batch, reps: int, flush=None):
     _check(_lib.heat_batch_profile_iteration(batch, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba),
                                              C.byref(bu)))
     return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_tuning_num_variants() -> int:
+    load_library()
+    return int(_lib.heat_tuning_num_variants())
+
+
+def heat_tuning_variant(v: int) -> dict:
+    load_library()
+    a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.heat_tuning_variant(int(v), C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return {"seg_width": a.value, "rows": b.value, "warps": c.value, "has_fp64": bool(d.value)}
+
+
+def heat_tuning_get() -> dict:
+    load_library()
+    t = heat_tuning()
+    _check(_lib.heat_tuning_get(C.byref(t)))
+    return t.as_dict()
+
+
+def heat_tuning_set(variant, seg_nodes):
+    load_library()
+    t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes))
+    _check(_lib.heat_tuning_set(C.byref(t)))
+
+
+def heat_autotune(sim, reps: int, flush=None):
+    """Tune the table for this sim's precision and size; returns (table, best ms per apply)."""
+    t = heat_tuning()
+    ms = C.c_double()
+    fp = C.c_void_p(_dev_ptr(flush)) if flush is not None else C.c_void_p(0)
+    fb = flush.numel() * flush.element_size() if flush is not None else 0
+    _check(_lib.heat_autotune(sim, int(reps), fp, fb, C.byref(t), C.byref(ms)))
+    return t.as_dict(), ms.value
 
 
 def heat_last_error() -> str:

@@ -8,7 +8,9 @@
 // unfinished simulations every few ticks (the paper's host reads the residual
 // back after every iteration, §3.4.3).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "engine.h"
@@ -26,31 +28,85 @@ struct KernelSet {
   TileFn apply_w;
   int wsx, wny, wwarps;
   int pw_chunk;  // nodes per pointwise (k_update) work item
+  int seg_nodes[3];  // warp-segment tile size per mesh-size bucket
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
   return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0,
-          pw_chunk<T>()};
+          pw_chunk<T>(), {512, 512, 512}};
 }
 
-template <int P, int SX, int SY, int WSX, int WNY, int WW>
-static KernelSet make_set_w() {
-  KernelSet k = make_set<P, SX, SY>();
-  k.apply_w = k_apply_dot_w<float, WSX, WNY, WW>;
-  k.wsx = WSX;
-  k.wny = WNY;
-  k.wwarps = WW;
-  return k;
+// Warp-segment apply variants the tuner chooses from (segment width, rows
+// per thread, warps per block); f64 is null where the FP64 registers do not fit.
+struct WVariant {
+  int sx, ny, warps;
+  TileFn f32, f64;
+};
+static const WVariant kVariants[] = {
+    {16, 4, 4, k_apply_dot_w<float, 16, 4, 4>, nullptr},
+    {32, 4, 4, k_apply_dot_w<float, 32, 4, 4>, nullptr},
+    {16, 2, 8, k_apply_dot_w<float, 16, 2, 8>, k_apply_dot_w<double, 16, 2, 8>},
+    {32, 2, 4, k_apply_dot_w<float, 32, 2, 4>, k_apply_dot_w<double, 32, 2, 4>},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+// Process-wide tuning table, read when an engine is created: the warp apply
+// variant per precision (-1: the block-tile apply) and the segment tile size
+// per mesh-size bucket. Both are fixed per simulation size, so results stay
+// bitwise identical alone and in batches built under the same table.
+static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}};
+static std::mutex g_tuning_mu;
+
+int num_variants() { return kNumVariants; }
+
+bool variant_info(int v, int info[4]) {
+  if (v < 0 || v >= kNumVariants) return false;
+  info[0] = kVariants[v].sx;
+  info[1] = kVariants[v].ny;
+  info[2] = kVariants[v].warps;
+  info[3] = kVariants[v].f64 != nullptr;
+  return true;
 }
 
-static KernelSet kernel_set(int prec) {
-  switch (prec) {
-    case P_FP64: return make_set<P_FP64, 16, 16>();
-    case P_FP32_REFINED: return make_set_w<P_FP32_REFINED, 16, 16, 16, 4, 4>();
-    default: return make_set_w<P_FP32_PLAIN, 16, 16, 16, 4, 4>();
+int size_bucket(long long nn) { return nn < 200000 ? 0 : (nn < 4000000 ? 1 : 2); }
+
+Tuning tuning_get() {
+  std::lock_guard<std::mutex> lock(g_tuning_mu);
+  return g_tuning;
+}
+
+heat_status tuning_set(const Tuning& t) {
+  for (int p = 0; p < 3; ++p) {
+    const int v = t.variant[p];
+    if (v < -1 || v >= kNumVariants || (v >= 0 && p == P_FP64 && !kVariants[v].f64))
+      return set_error(HEAT_ERR_ARG, "tuning: bad variant %d for precision %d", v, p);
   }
+  for (int b = 0; b < 3; ++b)
+    if (t.seg_nodes[b] < 32 || t.seg_nodes[b] > (1 << 20))
+      return set_error(HEAT_ERR_ARG, "tuning: segment size %d out of range", t.seg_nodes[b]);
+  std::lock_guard<std::mutex> lock(g_tuning_mu);
+  g_tuning = t;
+  return HEAT_OK;
+}
+
+static KernelSet kernel_set(int prec, const Tuning& t) {
+  const int variant = t.variant[prec];
+  KernelSet k = prec == P_FP64 ? make_set<P_FP64, 16, 16>()
+                               : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16>()
+                                                          : make_set<P_FP32_PLAIN, 16, 16>());
+  if (variant >= 0 && variant < kNumVariants) {
+    const WVariant& v = kVariants[variant];
+    k.apply_w = prec == P_FP64 ? v.f64 : v.f32;
+    if (k.apply_w) {
+      k.wsx = v.sx;
+      k.wny = v.ny;
+      k.wwarps = v.warps;
+    }
+  }
+  for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
+  return k;
 }
 
 // Number of simulations not yet DONE or FAILED.
@@ -120,11 +176,11 @@ static void tile_geometry(SimDev& d, const KernelSet& ks) {
   d.npw = (int)((d.nn + ks.pw_chunk - 1) / ks.pw_chunk);
   d.w_ntx = d.w_nty = d.w_ntz = d.w_tz = d.w_ntiles = d.w_items = 0;
   if (ks.apply_w) {
-    // segment tiles of about kSegNodes nodes, at least 4 levels (2 extra levels per tile)
-    constexpr int kSegNodes = 512;
+    // segment tiles of about seg output nodes, at least 4 levels (2 extra levels per tile)
+    const int seg = ks.seg_nodes[size_bucket(d.nn)];
     d.w_ntx = (d.nx + 1 + ks.wsx - 3) / (ks.wsx - 2);
     d.w_nty = (d.ny + 1 + ks.wny - 1) / ks.wny;
-    const int tz0 = std::max(4, std::min(levels, kSegNodes / ((ks.wsx - 2) * ks.wny)));
+    const int tz0 = std::max(4, std::min(levels, seg / ((ks.wsx - 2) * ks.wny)));
     d.w_ntz = (levels + tz0 - 1) / tz0;
     d.w_tz = (levels + d.w_ntz - 1) / d.w_ntz;
     d.w_ntiles = d.w_ntx * d.w_nty * d.w_ntz;
@@ -252,13 +308,14 @@ static heat_status engine_capture(Engine* e) {
   return HEAT_OK;
 }
 
-heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out) {
+heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out,
+                          const Tuning* tun) {
   *out = nullptr;
   if (nsims < 1 || !sims) return set_error(HEAT_ERR_ARG, "engine: no simulations");
   Engine* e = new Engine();
   e->sims.assign(sims, sims + nsims);
   e->prec = precision;
-  e->ks = kernel_set(precision);
+  e->ks = kernel_set(precision, tun ? *tun : tuning_get());
   e->stream = stream;
   // capacities: the geometry is a function of each mesh, so compute it
   long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_partial = 0;
@@ -440,10 +497,20 @@ heat_status engine_read_phases(Engine* e, int* phases) {
 long long engine_launches(const Engine* e) { return e->launches; }
 
 size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) {
-  const long long cols = (long long)((nx + 15 - 1) / 15 + 1) * ((ny + 15 - 1) / 15 + 1);  // 16x16 tiles, rounded up
-  const long long op = cols * (nz + 1);
-  const long long pw = (nn + 2047) / 2048;  // the smaller (FP64) chunk
-  const long long aw = (nn + 511) / 512 / 8 + 8;  // warp-apply items (8 segment tiles of ~512 nodes)
+  // the largest work lists any precision's kernels need under the current table
+  const Tuning t = tuning_get();
+  long long op = 0, pw = 0, aw = 0;
+  for (int p = 0; p < 3; ++p) {
+    SimDev d{};
+    d.nx = (int)nx;
+    d.ny = (int)ny;
+    d.nz = (int)nz;
+    d.nn = nn;
+    tile_geometry(d, kernel_set(p, t));
+    op = std::max<long long>(op, d.ntiles);
+    pw = std::max<long long>(pw, d.npw);
+    aw = std::max<long long>(aw, d.w_items);
+  }
   return (size_t)(sizeof(int2) * (op + pw + aw) + sizeof(double) * 4 * std::max(std::max(op, pw), aw) +
                   sizeof(SimDev) + 64);
 }
@@ -459,6 +526,23 @@ __global__ void k_flush_read(const uint4* __restrict__ p, size_t n, unsigned int
   if (acc == 0x9e3779b9u) *sink = acc;  // keeps the loads alive; practically never taken
 }
 
+// r[i] = a hash of i mapped to [-1, 1); *delta += sum r[i]^2 pinv[i].
+template <class T>
+__global__ void k_profile_seed(T* __restrict__ r, const T* __restrict__ pinv, long long n, double* delta) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned int h = (unsigned int)i * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    const T v = (T)((double)(h >> 8) * (1.0 / 8388608.0) - 1.0);
+    r[i] = v;
+    acc += (double)v * (double)v * (double)pinv[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(delta, acc);
+}
+
 heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
                            double* ms_update, double* bytes_apply, double* bytes_update) {
   const int chunk = 40;  // below the inner-solve cap and the true-residual period
@@ -466,9 +550,35 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   for (int i = 0; i < 4 * chunk; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
   double ta = 0.0, tu = 0.0;
   heat_status st = HEAT_OK;
+  // Every chunk restarts each member from the same well-scaled residual
+  // (pseudo-random entries in [-1, 1)) with delta = r^T P^-1 r computed for
+  // it, so the timed iterations are ordinary CG iterations whatever state the
+  // members were left in (a converged step leaves a residual near underflow).
+  double* d_delta = nullptr;
+  std::vector<double> h_delta(e->sims.size(), 0.0);
+  if (cudaMalloc(&d_delta, sizeof(double) * e->sims.size()) != cudaSuccess) {
+    cudaGetLastError();
+    st = set_error(HEAT_ERR_NOMEM, "profile: no room for the residual norms");
+  }
   for (int done = 0; done < reps && st == HEAT_OK;) {
     const int c = std::min(reps - done, chunk);
-    for (heat_sim* s : e->sims) {  // every member iterates, none converges
+    if (cudaMemsetAsync(d_delta, 0, sizeof(double) * e->sims.size(), e->stream) != cudaSuccess)
+      st = set_error(HEAT_ERR_CUDA, "profile: memset failed");
+    for (size_t i = 0; i < e->sims.size() && st == HEAT_OK; ++i) {
+      const heat_sim* s = e->sims[i];
+      const int g = (int)std::min<long long>((s->nn + 255) / 256, 4LL * sm_count());
+      if (e->prec == P_FP64)
+        k_profile_seed<double><<<g, 256, 0, e->stream>>>(s->dev.r, s->dev.pinv, s->nn, d_delta + i);
+      else
+        k_profile_seed<float><<<g, 256, 0, e->stream>>>(s->dev.r32, s->dev.pinv32, s->nn, d_delta + i);
+    }
+    if (st == HEAT_OK &&
+        (cudaMemcpyAsync(h_delta.data(), d_delta, sizeof(double) * e->sims.size(), cudaMemcpyDeviceToHost,
+                         e->stream) != cudaSuccess ||
+         cudaStreamSynchronize(e->stream) != cudaSuccess))
+      st = set_error(HEAT_ERR_CUDA, "profile: residual seeding failed");
+    for (size_t i = 0; i < e->sims.size() && st == HEAT_OK; ++i) {  // every member iterates, none converges
+      heat_sim* s = e->sims[i];
       st = sim_read_scalars(s);
       if (st != HEAT_OK) break;
       SimScalars* sc = s->h_sc;
@@ -479,7 +589,7 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
       sc->thresh = -1.0;
       sc->thresh_in = -1.0;
       sc->count = 0;
-      if (!(sc->delta > 0.0)) sc->delta = 1.0;
+      sc->delta = h_delta[i] > 0.0 ? h_delta[i] : 1.0;
       st = sim_write_scalars(s);
       if (st != HEAT_OK) break;
     }
@@ -521,6 +631,8 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
     done += c;
   }
   for (int i = 0; i < 4 * chunk; ++i) cudaEventDestroy(ev[i]);
+  cudaStreamSynchronize(e->stream);
+  cudaFree(d_delta);
   if (st != HEAT_OK) return st;
   *ms_apply = ta / reps;
   *ms_update = tu / reps;
@@ -538,6 +650,43 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   }
   *bytes_apply = ba;
   *bytes_update = bu;
+  return HEAT_OK;
+}
+
+heat_status engine_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, int* best_variant, int* best_seg,
+                            double* best_ms) {
+  static const int kSegs[] = {256, 512, 1024, 2048};
+  const int prec = sim->prm.precision;
+  const int bucket = size_bucket(sim->nn);
+  const Tuning base = tuning_get();
+  Tuning best = base;
+  double best_t = 1e300;
+  heat_status st = HEAT_OK;
+  for (int v = -1; v < kNumVariants && st == HEAT_OK; ++v) {
+    if (v >= 0 && prec == P_FP64 && !kVariants[v].f64) continue;
+    for (int si = 0; si < (v < 0 ? 1 : 4) && st == HEAT_OK; ++si) {
+      Tuning t = base;
+      t.variant[prec] = v;
+      if (v >= 0) t.seg_nodes[bucket] = kSegs[si];
+      Engine* e = nullptr;
+      st = engine_create(&sim, 1, prec, sim->stream, &e, &t);
+      if (st != HEAT_OK) break;
+      double ma = 0.0, mu = 0.0, ba = 0.0, bu = 0.0;
+      st = engine_profile(e, 3, flush, flush_bytes, &ma, &mu, &ba, &bu);  // warm-up
+      if (st == HEAT_OK) st = engine_profile(e, reps, flush, flush_bytes, &ma, &mu, &ba, &bu);
+      engine_destroy(e);
+      if (st == HEAT_OK && ma < best_t) {
+        best_t = ma;
+        best = t;
+      }
+    }
+  }
+  if (st != HEAT_OK) return st;
+  st = tuning_set(best);
+  if (st != HEAT_OK) return st;
+  *best_variant = best.variant[prec];
+  *best_seg = best.seg_nodes[bucket];
+  *best_ms = best_t;
   return HEAT_OK;
 }
 

@@ -52,8 +52,27 @@ size_t sim_footprint(long long nn, long long ne);
 // Statistics from the host copy of the scalars (after sim_read_scalars).
 void sim_stats(const heat_sim* s, heat_step_stats* o);
 
-// A set of simulations driven together by one captured tick graph.
-heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out);
+// Kernel tuning: warp-apply variant per precision (-1: block-tile apply) and
+// segment tile size (nodes) per mesh-size bucket (size_bucket).
+struct Tuning {
+  int variant[3];
+  int seg_nodes[3];
+};
+int size_bucket(long long nn);
+int num_variants();
+// {segment width, rows per thread, warps per block, has an FP64 kernel}
+bool variant_info(int v, int info[4]);
+Tuning tuning_get();
+heat_status tuning_set(const Tuning& t);
+// Time the apply kernel of every candidate (variant, segment size) on `sim`
+// (which must have run a step) and store the fastest in the table.
+heat_status engine_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, int* best_variant, int* best_seg,
+                            double* best_ms);
+
+// A set of simulations driven together by one captured tick graph (kernel
+// choice from the tuning table, or from `tun` when given).
+heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out,
+                          const Tuning* tun = nullptr);
 void engine_destroy(Engine* e);
 // Re-read the sims' descriptors (after a buffer or parameter change).
 heat_status engine_refresh(Engine* e);

@@ -671,3 +671,52 @@ extern "C" heat_status heat_profile_iteration(heat_sim* s, int reps, void* flush
   if (!s->eng) return set_error(HEAT_ERR_ARG, "heat_profile_iteration: call heat_step first");
   return engine_profile(s->eng, reps, flush, flush_bytes, ms_apply, ms_update, bytes_apply, bytes_update);
 }
+
+// ------------------------------------------------------------ kernel tuning
+
+extern "C" int heat_tuning_num_variants(void) { return num_variants(); }
+
+extern "C" heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64) {
+  int info[4];
+  if (!variant_info(v, info)) return set_error(HEAT_ERR_ARG, "heat_tuning_variant: unknown variant %d", v);
+  if (seg_width) *seg_width = info[0];
+  if (rows) *rows = info[1];
+  if (warps) *warps = info[2];
+  if (has_fp64) *has_fp64 = info[3];
+  return HEAT_OK;
+}
+
+extern "C" heat_status heat_tuning_get(heat_tuning* t) {
+  if (!t) return set_error(HEAT_ERR_ARG, "heat_tuning_get: null argument");
+  const Tuning x = tuning_get();
+  for (int i = 0; i < 3; ++i) {
+    t->variant[i] = x.variant[i];
+    t->seg_nodes[i] = x.seg_nodes[i];
+  }
+  return HEAT_OK;
+}
+
+extern "C" heat_status heat_tuning_set(const heat_tuning* t) {
+  if (!t) return set_error(HEAT_ERR_ARG, "heat_tuning_set: null argument");
+  Tuning x;
+  for (int i = 0; i < 3; ++i) {
+    x.variant[i] = t->variant[i];
+    x.seg_nodes[i] = t->seg_nodes[i];
+  }
+  return tuning_set(x);
+}
+
+extern "C" heat_status heat_autotune(heat_sim* s, int reps, void* flush, size_t flush_bytes, heat_tuning* best,
+                                     double* best_ms) {
+  if (!s || reps < 1) return set_error(HEAT_ERR_ARG, "heat_autotune: bad argument");
+  if (!s->eng) return set_error(HEAT_ERR_ARG, "heat_autotune: call heat_step first");
+  int v = 0, seg = 0;
+  double ms = 0.0;
+  heat_status st = engine_autotune(s, reps, flush, flush_bytes, &v, &seg, &ms);
+  if (st != HEAT_OK) return st;
+  engine_destroy(s->eng);  // rebuilt under the new table by the next heat_step
+  s->eng = nullptr;
+  if (best) st = heat_tuning_get(best);
+  if (best_ms) *best_ms = ms;
+  return st;
+}

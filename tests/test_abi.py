@@ -70,3 +70,32 @@ def test_server_create_fails_cleanly_without_a_device(lib):
     with pytest.raises(api.HeatError) as e:
         api.heat_server_create(1 << 30, 4)
     assert e.value.status == api.HEAT_ERR_CUDA
+
+
+def test_tuning_table_host_logic(lib):
+    import paper_1905_07622_gb300.api as api
+
+    n = api.heat_tuning_num_variants()
+    assert n >= 2
+    shapes = [api.heat_tuning_variant(v) for v in range(n)]
+    assert all(s["seg_width"] in (16, 32) and s["rows"] >= 1 and s["warps"] >= 1 for s in shapes)
+    with pytest.raises(api.HeatError):
+        api.heat_tuning_variant(n)
+    old = api.heat_tuning_get()
+    assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512]}
+    try:
+        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048])
+        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048]}
+        no64 = [v for v in range(n) if not shapes[v]["has_fp64"]]
+        bad = [([-1, n, 0], [512] * 3), ([-2, 0, 0], [512] * 3), ([-1, 0, 0], [16, 512, 512]),
+               ([-1, 0, 0], [512, 512, (1 << 20) + 1])]
+        if no64:
+            bad.append(([no64[0], 0, 0], [512] * 3))
+        for variant, seg in bad:
+            with pytest.raises(api.HeatError) as e:
+                api.heat_tuning_set(variant, seg)
+            assert e.value.status == api.HEAT_ERR_ARG
+        # a rejected table leaves the last good one in place
+        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048]}
+    finally:
+        api.heat_tuning_set(old["variant"], old["seg_nodes"])

@@ -313,9 +313,11 @@ typedef struct heat_tuning {
 } heat_tuning;
 int heat_tuning_num_variants(void);
 /* Shape of variant v: segment width in nodes along x (one lane per node),
- * element rows along y per lane, warps per block, and whether an FP64 kernel
- * exists. HEAT_ERR_ARG for an unknown v. */
-heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64);
+ * node rows along y per lane, warps per block, whether an FP64 kernel exists,
+ * and how its loads travel: 0 = plain loads one level ahead into registers,
+ * S >= 2 = each thread's own cp.async copies S-1 levels ahead into an S-stage
+ * ring in shared memory. Any output may be NULL. HEAT_ERR_ARG for an unknown v. */
+heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64, int* stages);
 heat_status heat_tuning_get(heat_tuning* t);
 /* HEAT_ERR_ARG (table unchanged) for an unknown variant, a variant without
  * an FP64 kernel in variant[HEAT_FP64], or a segment size out of range. */

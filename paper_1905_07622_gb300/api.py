@@ -124,7 +124,7 @@ _SIGS = [
                                          _VP, _VP, _VP, _VP, _VP]),
     ("heat_tuning_num_variants", C.c_int, []),
     ("heat_tuning_variant", C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                      C.POINTER(C.c_int)]),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("heat_tuning_get", C.c_int, [C.POINTER(heat_tuning)]),
     ("heat_tuning_set", C.c_int, [C.POINTER(heat_tuning)]),
     ("heat_autotune", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, C.POINTER(heat_tuning), _DP]),
@@ -463,9 +463,9 @@ def heat_tuning_num_variants() -> int:
 
 def heat_tuning_variant(v: int) -> dict:
     load_library()
-    a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-    _check(_lib.heat_tuning_variant(int(v), C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
-    return {"seg_width": a.value, "rows": b.value, "warps": c.value, "has_fp64": bool(d.value)}
+    a, b, c, d, e = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.heat_tuning_variant(int(v), C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e)))
+    return {"seg_width": a.value, "rows": b.value, "warps": c.value, "has_fp64": bool(d.value), "stages": e.value}
 
 
 def heat_tuning_get() -> dict:

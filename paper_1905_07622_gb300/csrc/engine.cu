@@ -29,26 +29,41 @@ struct KernelSet {
   int wsx, wny, wwarps;
   int pw_chunk;  // nodes per pointwise (k_update) work item
   int seg_nodes[3];  // warp-segment tile size per mesh-size bucket
+  int apply_w_smem;  // dynamic shared memory of apply_w per block
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
   return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0,
-          pw_chunk<T>(), {512, 512, 512}};
+          pw_chunk<T>(), {512, 512, 512}, 0};
 }
 
-// Warp-segment apply variants the tuner chooses from (segment width, rows
-// per thread, warps per block); f64 is null where the FP64 registers do not fit.
+// Warp-segment apply variants the tuner chooses from: segment width, rows per
+// lane, warps per block, cp.async stages (0: register prefetch); f64 is null
+// where the FP64 registers or shared memory do not fit.
 struct WVariant {
-  int sx, ny, warps;
+  int sx, ny, warps, stages;
   TileFn f32, f64;
+  int smem32, smem64;  // dynamic shared memory per block
 };
+template <class T, int SX, int NY, int W, int S, int MINB, bool ON>
+static constexpr TileFn wfn() {
+  if constexpr (ON) return k_apply_dot_w<T, SX, NY, W, S, MINB>;
+  else return nullptr;
+}
+template <int SX, int NY, int W, int S, int MINB, int MINB64>
+static constexpr WVariant wv() {
+  return {SX, NY, W, S, wfn<float, SX, NY, W, S, MINB, true>(), wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0)>(),
+          S ? 32 * W * async_stage_bytes<float, NY, (S ? S : 2)>() : 0,
+          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0};
+}
+// (segment width, rows, warps, stages, min blocks per SM for float / double,
+// 0 = no double kernel)
 static const WVariant kVariants[] = {
-    {16, 4, 4, k_apply_dot_w<float, 16, 4, 4>, nullptr},
-    {32, 4, 4, k_apply_dot_w<float, 32, 4, 4>, nullptr},
-    {16, 2, 8, k_apply_dot_w<float, 16, 2, 8>, k_apply_dot_w<double, 16, 2, 8>},
-    {32, 2, 4, k_apply_dot_w<float, 32, 2, 4>, k_apply_dot_w<double, 32, 2, 4>},
+    wv<16, 4, 4, 0, 3, 0>(), wv<32, 4, 4, 0, 3, 0>(), wv<16, 2, 8, 0, 2, 1>(), wv<32, 2, 4, 0, 4, 1>(),
+    wv<16, 4, 4, 3, 4, 0>(), wv<32, 4, 4, 3, 4, 0>(), wv<16, 2, 8, 3, 2, 1>(), wv<32, 4, 4, 3, 3, 0>(),
+    wv<32, 4, 4, 4, 3, 0>(),
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -61,12 +76,13 @@ static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }
 
-bool variant_info(int v, int info[4]) {
+bool variant_info(int v, int info[5]) {
   if (v < 0 || v >= kNumVariants) return false;
   info[0] = kVariants[v].sx;
   info[1] = kVariants[v].ny;
   info[2] = kVariants[v].warps;
   info[3] = kVariants[v].f64 != nullptr;
+  info[4] = kVariants[v].stages;
   return true;
 }
 
@@ -103,6 +119,9 @@ static KernelSet kernel_set(int prec, const Tuning& t) {
       k.wsx = v.sx;
       k.wny = v.ny;
       k.wwarps = v.warps;
+      k.apply_w_smem = prec == P_FP64 ? v.smem64 : v.smem32;
+      if (k.apply_w_smem > 0)
+        cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
     }
   }
   for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
@@ -231,7 +250,8 @@ static heat_status engine_upload(Engine* e) {
   int occ_op = 1, occ_pw = 1, occ_aw = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_op, e->ks.apply, e->ks.apply_threads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pw, e->ks.update, kPwThreads, 0);
-  if (e->ks.apply_w) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_aw, e->ks.apply_w, 32 * e->ks.wwarps, 0);
+  if (e->ks.apply_w)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_aw, e->ks.apply_w, 32 * e->ks.wwarps, e->ks.apply_w_smem);
   e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
   e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
   e->grid_aw = (int)std::max(1LL, std::min<long long>(nwork[2], (long long)sms * std::max(1, occ_aw)));
@@ -240,8 +260,10 @@ static heat_status engine_upload(Engine* e) {
 
 // The apply kernel of an iteration and its launch shape / work list.
 static void apply_launch(const Engine* e, TileFn* fn, int* grid, int* threads, const int2** work,
-                         const int** nwork) {
+                         const int** nwork, int* smem) {
+  *smem = 0;
   if (e->ks.apply_w) {
+    *smem = e->ks.apply_w_smem;
     *fn = e->ks.apply_w;
     *grid = e->grid_aw;
     *threads = 32 * e->ks.wwarps;
@@ -272,10 +294,11 @@ static heat_status engine_capture(Engine* e) {
   // Each kernel may launch while its predecessor finishes (programmatic
   // dependent launch); the kernels wait for the predecessor's results with
   // cudaGridDependencySynchronize after their static prologue.
-  auto launch = [&](TileFn fn, int grid, int block, const int2* work, const int* nwork) -> cudaError_t {
+  auto launch = [&](TileFn fn, int grid, int block, const int2* work, const int* nwork, int smem) -> cudaError_t {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = cap;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -285,16 +308,17 @@ static heat_status engine_capture(Engine* e) {
     return cudaLaunchKernelEx(&cfg, fn, (const SimDev*)e->d_sims, work, nwork);
   };
   TileFn afn;
-  int agrid, athreads;
+  int agrid, athreads, asmem;
   const int2* awork;
   const int* anwork;
-  apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork);
+  apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork, &asmem);
   cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
-    cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork);
+    cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
     for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
-      lerr = launch(afn, agrid, athreads, awork, anwork);
-      if (lerr == cudaSuccess) lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1);
+      lerr = launch(afn, agrid, athreads, awork, anwork, asmem);
+      if (lerr == cudaSuccess)
+        lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1, 0);
     }
     err = cudaStreamEndCapture(cap, &e->graph);
     if (err == cudaSuccess && lerr != cudaSuccess) err = lerr;
@@ -599,11 +623,11 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
       cudaEventRecord(ev[4 * i + 0], e->stream);
       {
         TileFn afn;
-        int agrid, athreads;
+        int agrid, athreads, asmem;
         const int2* awork;
         const int* anwork;
-        apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork);
-        afn<<<agrid, athreads, 0, e->stream>>>(e->d_sims, awork, anwork);
+        apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork, &asmem);
+        afn<<<agrid, athreads, asmem, e->stream>>>(e->d_sims, awork, anwork);
       }
       cudaEventRecord(ev[4 * i + 1], e->stream);
       if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);

@@ -60,8 +60,8 @@ struct Tuning {
 };
 int size_bucket(long long nn);
 int num_variants();
-// {segment width, rows per thread, warps per block, has an FP64 kernel}
-bool variant_info(int v, int info[4]);
+// {segment width, rows per thread, warps per block, has an FP64 kernel, cp.async stages}
+bool variant_info(int v, int info[5]);
 Tuning tuning_get();
 heat_status tuning_set(const Tuning& t);
 // Time the apply kernel of every candidate (variant, segment size) on `sim`

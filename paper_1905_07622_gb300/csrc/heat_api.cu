@@ -676,13 +676,15 @@ extern "C" heat_status heat_profile_iteration(heat_sim* s, int reps, void* flush
 
 extern "C" int heat_tuning_num_variants(void) { return num_variants(); }
 
-extern "C" heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64) {
-  int info[4];
+extern "C" heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64,
+                                           int* stages) {
+  int info[5];
   if (!variant_info(v, info)) return set_error(HEAT_ERR_ARG, "heat_tuning_variant: unknown variant %d", v);
   if (seg_width) *seg_width = info[0];
   if (rows) *rows = info[1];
   if (warps) *warps = info[2];
   if (has_fp64) *has_fp64 = info[3];
+  if (stages) *stages = info[4];
   return HEAT_OK;
 }
 

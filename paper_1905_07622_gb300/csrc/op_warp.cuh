@@ -5,145 +5,330 @@
 // thread holds NY+2 consecutive y rows of its column and marches up the z
 // levels. Forward x and the final x-sum use segment shuffles; forward y,
 // forward z, scaling, inverse z, the face sums and inverse y all stay in the
-// thread's registers, so the level loop has no shared memory and no barrier,
-// and the NY rows are independent instruction streams. Outputs are lanes
-// 1..SX-2 (the outer lanes only supply neighbours), rows 1..NY, levels
-// [k0, k0+nzt): (SX-2) x NY x nzt nodes per segment.
+// thread's registers, so the level loop has no block barrier, and the NY rows
+// are independent instruction streams. Outputs are lanes 1..SX-2 (the outer
+// lanes only supply neighbours), rows 1..NY, levels [k0, k0+nzt):
+// (SX-2) x NY x nzt nodes per segment.
+//
+// Where the loads come from is a policy (the Src argument):
+//  - RegSrc: plain loads one level ahead into registers;
+//  - AsyncSrc: each thread copies its own rows S-1 levels ahead into a
+//    private ring of S stages in shared memory with cp.async (no registers held
+//    for data in flight, no barrier: a thread reads back only what it copied,
+//    after waiting for its own copy groups).
 #pragma once
+
+#include <utility>
 
 #include "op.cuh"
 
 namespace heat {
 
+// Pairs of values with element-wise arithmetic: packed FP32x2 instructions for
+// float (two results per issued instruction on sm_100 and later), two scalar
+// operations for double. fma(a, b, c) = a*b + c with one rounding per lane.
+template <class T> struct Pair2;
+template <> struct Pair2<float> {
+  using t = float2;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pair2<double> {
+  using t = double2;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+  static __device__ __forceinline__ double2 fma(double2 a, double2 b, double2 c) {
+    return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+  }
+};
+
+// Geometry of one lane of a segment tile: which of its rows exist, which are
+// Dirichlet, where its column starts.
+template <int NY>
+struct LaneGeo {
+  static constexpr int NR = NY + 2;  // staged rows
+  static constexpr int NF = NY + 1;  // faces / element rows
+  bool out_lane;
+  unsigned rin, rdxy, ein, rstat;  // bit r: row inside / x-y Dirichlet / element row valid / loadable
+  int nbase, ebase, estride, pxy, gnz, px, enx;
+  bool dz0, dz1, mask;
+
+  __device__ __forceinline__ LaneGeo(const Geo& g, bool active, int lx, int SX, int i0, int j0, bool mask_) {
+    const int c = i0 - 1 + lx;
+    const bool col_in = active && c >= 0 && c <= g.nx;
+    out_lane = active && lx >= 1 && lx <= SX - 2 && c <= g.nx;
+    const bool ecol = active && c >= 0 && c < g.nx;
+    const bool dx = col_in && (((g.dir & 1u) && c == 0) || ((g.dir & 2u) && c == g.nx));
+    rin = rdxy = ein = 0u;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int j = j0 - 1 + r;
+      const bool in = col_in && j >= 0 && j <= g.ny;
+      if (in) rin |= 1u << r;
+      if (in && (dx || ((g.dir & 4u) && j == 0) || ((g.dir & 8u) && j == g.ny))) rdxy |= 1u << r;
+      if (r < NF && ecol && j >= 0 && j < g.ny) ein |= 1u << r;
+    }
+    nbase = c + g.px * (j0 - 1);  // node index of row 0 at level 0 (rows step by px)
+    ebase = c + g.nx * (j0 - 1);  // element index of element row 0 at level 0
+    estride = g.nx * g.ny;
+    pxy = g.pxy;
+    gnz = g.nz;
+    px = g.px;
+    enx = g.nx;
+    dz0 = (g.dir & 16u) != 0;
+    dz1 = (g.dir & 32u) != 0;
+    mask = mask_;
+    rstat = rin & ~(mask ? rdxy : 0u);  // rows that can be live at any level
+  }
+  // rows of node level L that hold unknowns (bit r)
+  __device__ __forceinline__ unsigned live_rows(int L) const {
+    const bool lev = L >= 0 && L <= gnz && !(mask && ((dz0 && L == 0) || (dz1 && L == gnz)));
+    return lev ? rstat : 0u;
+  }
+  // element rows of element layer E inside the mesh (bit r)
+  __device__ __forceinline__ unsigned live_elems(int E) const { return (E >= 0 && E < gnz) ? ein : 0u; }
+};
+
+// Loads one level ahead into registers through caller-supplied functors:
+// fetch(node, live) -> Raw, value(Raw) -> T.
+template <class T, int NY, class Coef, class Fetch, class Value>
+struct RegSrc {
+  static constexpr int NR = NY + 2, NF = NY + 1;
+  using Raw = decltype(std::declval<Fetch&>()(0, false));
+  const Coef* __restrict__ coef;
+  Fetch& fetch;
+  Value& value;
+  int k0;
+  Raw raw[NR];
+  Coef cf[NF];
+
+  __device__ __forceinline__ RegSrc(const Coef* c, Fetch& f, Value& v, int k0_) : coef(c), fetch(f), value(v), k0(k0_) {}
+  __device__ __forceinline__ void load_nodes(const LaneGeo<NY>& lg, int L) {
+    const unsigned lv = lg.live_rows(L);
+    const int off = lg.nbase + L * lg.pxy;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) raw[r] = fetch(off + r * lg.px, (lv >> r) & 1u);
+  }
+  __device__ __forceinline__ void load_coef(const LaneGeo<NY>& lg, int E) {
+    const unsigned le = lg.live_elems(E);
+#pragma unroll
+    for (int r = 0; r < NF; ++r) {
+      Coef z;
+      z.x = T(0);
+      z.y = T(0);
+      cf[r] = ((le >> r) & 1u) ? coef[lg.ebase + r * lg.enx + E * lg.estride] : z;
+    }
+  }
+  // before the loop: node level k0-1, element layer k0-1 (used at t = 1)
+  __device__ __forceinline__ void prologue(const LaneGeo<NY>& lg, int) {
+    load_nodes(lg, k0 - 1);
+    load_coef(lg, k0 - 1);
+  }
+  // values of node level L = k0-1+t, then the next level's loads
+  __device__ __forceinline__ void level(const LaneGeo<NY>& lg, int t, int tzl, T v[NR]) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = value(raw[r]);
+    if (t <= tzl) load_nodes(lg, k0 + t);  // in flight during this level's arithmetic
+  }
+  // coefficients of element layer k0-2+t (valid for t >= 1)
+  __device__ __forceinline__ Coef coef_row(int, int r) const { return cf[r]; }
+  __device__ __forceinline__ void after_elements(const LaneGeo<NY>& lg, int t, int tzl) {
+    if (t <= tzl) load_coef(lg, k0 - 1 + t);
+  }
+};
+
+// cp.async of 4, 8 or 16 bytes into shared memory; live = false writes zeros
+// and reads nothing (the source address must still be a valid pointer).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool live) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = live ? BYTES : 0;
+  if (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+  else if (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory bytes one thread of AsyncSrc<T, NY, S> uses.
+template <class T, int NY, int S>
+__host__ __device__ constexpr int async_stage_bytes() {
+  return S * ((NY + 2) * 3 * (int)sizeof(T) + (NY + 1) * 2 * (int)sizeof(T));
+}
+
+// The direction-fused apply's loads (P^-1, r, d_old per node; (rho_c, k) per
+// element) staged through a per-thread ring of S stages. Stage t holds node
+// level k0-1+t and element layer k0-2+t. Layout: planes of nt values (one per
+// thread of the block), so a warp's accesses are conflict-free.
+template <class T, int NY, int S, class Coef>
+struct AsyncSrc {
+  static constexpr int NR = NY + 2, NF = NY + 1;
+  static_assert(S >= 2, "at least two stages");
+  const T* __restrict__ pinv;
+  const T* __restrict__ r;
+  const T* __restrict__ dold;  // nullptr: restart, d_old = 0
+  const Coef* __restrict__ coef;
+  T beta;
+  T* nodes;     // [S][NR][3][nt]
+  Coef* elems;  // [S][NF][nt]
+  int nt, tid, k0;
+
+  __device__ __forceinline__ AsyncSrc(const T* p, const T* rr, const T* d, const Coef* c, T b, void* smem, int nthreads,
+                                      int thread, int k0_)
+      : pinv(p), r(rr), dold(d), coef(c), beta(b), nt(nthreads), tid(thread), k0(k0_) {
+    nodes = reinterpret_cast<T*>(smem);
+    elems = reinterpret_cast<Coef*>(nodes + S * NR * 3 * nt);
+  }
+  __device__ __forceinline__ T* node_slot(int st, int row, int comp) const {
+    return nodes + ((st * NR + row) * 3 + comp) * nt + tid;
+  }
+  __device__ __forceinline__ Coef* elem_slot(int st, int row) const { return elems + (st * NF + row) * nt + tid; }
+
+  // copies for stage t (node level k0-1+t, element layer k0-2+t) as one group
+  __device__ __forceinline__ void issue(const LaneGeo<NY>& lg, int t) {
+    const int st = t % S;
+    const int L = k0 - 1 + t, E = L - 1;
+    const unsigned lv = lg.live_rows(L);
+    const int off = lg.nbase + L * lg.pxy;
+#pragma unroll
+    for (int row = 0; row < NR; ++row) {
+      const bool live = (lv >> row) & 1u;
+      const int m = live ? off + row * lg.px : 0;
+      cp_async<sizeof(T)>(node_slot(st, row, 0), pinv + m, live);
+      cp_async<sizeof(T)>(node_slot(st, row, 1), r + m, live);
+      if (dold) cp_async<sizeof(T)>(node_slot(st, row, 2), dold + m, live);
+    }
+    const unsigned le = lg.live_elems(E);
+#pragma unroll
+    for (int row = 0; row < NF; ++row) {
+      const bool live = (le >> row) & 1u;
+      const int e = live ? lg.ebase + row * lg.enx + E * lg.estride : 0;
+      cp_async<sizeof(Coef)>(elem_slot(st, row), coef + e, live);
+    }
+    cp_async_commit();
+  }
+  __device__ __forceinline__ void prologue(const LaneGeo<NY>& lg, int tzl) {
+#pragma unroll
+    for (int t = 0; t < S - 1; ++t) {
+      if (t <= tzl + 1) issue(lg, t);
+      else cp_async_commit();  // one group per stage keeps the wait count fixed
+    }
+  }
+  __device__ __forceinline__ void level(const LaneGeo<NY>& lg, int t, int tzl, T v[NR]) {
+    // stage t+S-1 reuses the slot of stage t-1, which the previous level consumed
+    if (t + S - 1 <= tzl + 1) issue(lg, t + S - 1);
+    else cp_async_commit();
+    cp_async_wait<S - 1>();  // stage t has landed
+    const int st = t % S;
+#pragma unroll
+    for (int row = 0; row < NR; ++row) {
+      const T p = *node_slot(st, row, 0), rv = *node_slot(st, row, 1);
+      const T d = dold ? *node_slot(st, row, 2) : T(0);
+      v[row] = p * rv + beta * d;
+    }
+  }
+  __device__ __forceinline__ Coef coef_row(int t, int row) const { return *elem_slot(t % S, row); }
+  __device__ __forceinline__ void after_elements(const LaneGeo<NY>&, int, int) {}
+};
+
 // Every lane of the segment must call this with the same tzl (the trip count
 // of the level loop): shuffles span the segment. Segments with no tile pass
 // active = false (they load and store nothing). Levels beyond the mesh are
-// zero; outputs are clipped to the mesh.
-template <class T, int SX, int NY, class Coef, class Fetch, class Value, class Out>
-__device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, const Coef* __restrict__ coef, bool active,
-                                             int i0, int j0, int k0, int tzl, T sa, T sb, bool mask, Fetch&& fetch,
-                                             Value&& value, Out&& out) {
+// zero; outputs are clipped to the mesh. out(node, dirichlet, y, v) receives
+// the operator output y and the node's own input value v.
+template <class T, int SX, int NY, class Src, class Out>
+__device__ __forceinline__ void warp_tile_march(const LaneGeo<NY>& lg, const SimDev& s, Src& src, int tzl, T sa,
+                                                T sb, Out&& out) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int NR = NY + 2;  // staged rows
   constexpr int NF = NY + 1;  // faces / element rows
-  const int lx = (int)threadIdx.x % SX;
-  const int c = i0 - 1 + lx;
-  const bool col_in = active && c >= 0 && c <= g.nx;
-  const bool out_lane = active && lx >= 1 && lx <= SX - 2 && c <= g.nx;
-  const bool ecol = active && c >= 0 && c < g.nx;
-  const bool dx = col_in && (((g.dir & 1u) && c == 0) || ((g.dir & 2u) && c == g.nx));
-  // per-row flags (bit r): inside the mesh, on an x/y Dirichlet face, element row valid
-  unsigned rin = 0u, rdxy = 0u, ein = 0u;
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int j = j0 - 1 + r;
-    const bool in = col_in && j >= 0 && j <= g.ny;
-    if (in) rin |= 1u << r;
-    if (in && (dx || ((g.dir & 4u) && j == 0) || ((g.dir & 8u) && j == g.ny))) rdxy |= 1u << r;
-    if (r < NF && ecol && j >= 0 && j < g.ny) ein |= 1u << r;
-  }
-  const int nbase = c + g.px * (j0 - 1);  // node index of row 0 at level 0 (rows step by px)
-  const int ebase = c + g.nx * (j0 - 1);  // element index of element row 0 at level 0
-  const int estride = g.nx * g.ny, pxy = g.pxy, gnz = g.nz, px = g.px, enx = g.nx;
-  const bool dz0 = (g.dir & 16u) != 0, dz1 = (g.dir & 32u) != 0;
   // With lam_q and lam'_q = lam_{q+4} (the two z-Walsh indices of an xy index
   // q), the face sum and the element's top half are
   //   G_q = Tp_q + A_q Fp_q + B_q F_q,  Tn_q = B_q Fp_q + A_q F_q,
   //   A_q = lam_q + lam'_q,  B_q = lam_q - lam'_q,
-  // and A_q, B_q are linear in (rho_c, k) with these coefficients:
-  T am[4], ak[4], bm[4], bk[4];
+  // and A_q, B_q are linear in (rho_c, k) with these coefficients. The four
+  // xy indices are processed as two pairs, h = 0: q = (0, 1), h = 1: q = (2, 3).
+  using V = Pair2<T>;
+  using T2 = typename V::t;
+  T2 AM[2], AK[2], BM[2], BK[2];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    am[q] = sa * (lam_m<T>(s, q) + lam_m<T>(s, q + 4));
-    ak[q] = sb * (lam_k<T>(s, q) + lam_k<T>(s, q + 4));
-    bm[q] = sa * (lam_m<T>(s, q) - lam_m<T>(s, q + 4));
-    bk[q] = sb * (lam_k<T>(s, q) - lam_k<T>(s, q + 4));
+  for (int h = 0; h < 2; ++h) {
+    const int q0 = 2 * h, q1 = 2 * h + 1;
+    AM[h] = V::make(sa * (lam_m<T>(s, q0) + lam_m<T>(s, q0 + 4)), sa * (lam_m<T>(s, q1) + lam_m<T>(s, q1 + 4)));
+    AK[h] = V::make(sb * (lam_k<T>(s, q0) + lam_k<T>(s, q0 + 4)), sb * (lam_k<T>(s, q1) + lam_k<T>(s, q1 + 4)));
+    BM[h] = V::make(sa * (lam_m<T>(s, q0) - lam_m<T>(s, q0 + 4)), sa * (lam_m<T>(s, q1) - lam_m<T>(s, q1 + 4)));
+    BK[h] = V::make(sb * (lam_k<T>(s, q0) - lam_k<T>(s, q0 + 4)), sb * (lam_k<T>(s, q1) - lam_k<T>(s, q1 + 4)));
   }
-  using Raw = decltype(fetch(0, false));
-  using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
-  Raw raw[NR];
-  CoefT cf[NF];
-  const unsigned rstat = rin & ~(mask ? rdxy : 0u);  // rows that can be live at any level
-  auto fetch_level = [&](int L) {
-    const bool lev = L >= 0 && L <= gnz && !(mask && ((dz0 && L == 0) || (dz1 && L == gnz)));
-    const unsigned lv = lev ? rstat : 0u;
-    const int off = nbase + L * pxy;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) raw[r] = fetch(off + r * px, (lv >> r) & 1u);
-  };
-  auto fetch_coef = [&](int E) {
-    const bool ek = E >= 0 && E < gnz;
-#pragma unroll
-    for (int r = 0; r < NF; ++r) {
-      CoefT z;
-      z.x = T(0);
-      z.y = T(0);
-      cf[r] = (ek && ((ein >> r) & 1u)) ? coef[ebase + r * enx + E * estride] : z;
-    }
-  };
-  fetch_level(k0 - 1);
-  fetch_coef(k0 - 1);
-  T Fp[NF][4], Tp[NF][4], vprev[NY];
+  const T2 M1 = V::make(T(-1), T(-1));  // a - b = fma(b, M1, a), exact as a subtraction
+  src.prologue(lg, tzl);
+  T2 Fp[NF][2], Tp[NF][2];
+  T vprev[NY];
 #pragma unroll
   for (int r = 0; r < NF; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Fp[r][q] = T(0);
-      Tp[r][q] = T(0);
+    for (int h = 0; h < 2; ++h) {
+      Fp[r][h] = V::make(T(0), T(0));
+      Tp[r][h] = V::make(T(0), T(0));
     }
 #pragma unroll
   for (int r = 0; r < NY; ++r) vprev[r] = T(0);
 
+  const int k0 = src.k0;
   for (int t = 0; t <= tzl + 1; ++t) {
     const int L = k0 - 1 + t;
     T v[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = value(raw[r]);
-    if (t <= tzl) fetch_level(L + 1);  // next level's loads in flight during this one
-    // forward x (edges of each row) and forward y (faces between rows)
-    T e0[NR], e1[NR];
+    src.level(lg, t, tzl, v);
+    // forward x (edges of each row, as the pair (sum, difference)) and
+    // forward y (faces between rows): F[r][0] = (F_0, F_1), F[r][1] = (F_2, F_3)
+    T2 E[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       const T vr = __shfl_down_sync(FULL, v[r], 1, SX);
-      e0[r] = v[r] + vr;
-      e1[r] = v[r] - vr;
+      E[r] = V::make(v[r] + vr, v[r] - vr);
     }
-    T F[NF][4];
+    T2 F[NF][2];
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
-      F[r][0] = e0[r] + e0[r + 1];
-      F[r][1] = e1[r] + e1[r + 1];
-      F[r][2] = e0[r] - e0[r + 1];
-      F[r][3] = e1[r] - e1[r + 1];
+      F[r][0] = V::add(E[r], E[r + 1]);
+      F[r][1] = V::fma(E[r + 1], M1, E[r]);
     }
     if (t >= 1) {
       // elements (c, j0-1+r, L-1) between face levels L-1 and L
-      T G[NF][4];
+      T2 G[NF][2];
 #pragma unroll
       for (int r = 0; r < NF; ++r) {
-        const T rc = cf[r].x, kc = cf[r].y;
+        const auto cf = src.coef_row(t, r);
+        const T2 rc = V::make(cf.x, cf.x), kc = V::make(cf.y, cf.y);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T A = rc * am[q] + kc * ak[q], B = rc * bm[q] + kc * bk[q];
-          G[r][q] = Tp[r][q] + A * Fp[r][q] + B * F[r][q];
-          Tp[r][q] = B * Fp[r][q] + A * F[r][q];
+        for (int h = 0; h < 2; ++h) {
+          const T2 A = V::fma(kc, AK[h], V::mul(rc, AM[h]));
+          const T2 B = V::fma(kc, BK[h], V::mul(rc, BM[h]));
+          G[r][h] = V::fma(B, F[r][h], V::fma(A, Fp[r][h], Tp[r][h]));
+          Tp[r][h] = V::fma(A, F[r][h], V::mul(B, Fp[r][h]));
         }
       }
-      if (t <= tzl) fetch_coef(L);
+      src.after_elements(lg, t, tzl);
       if (t >= 2) {
         // node level L-1 is complete: inverse y, inverse x, x-sum
         const int lv = L - 1;
-        const bool lvin = lv <= gnz;
-        const bool dzl = (dz0 && lv == 0) || (dz1 && lv == gnz);
+        const bool lvin = lv <= lg.gnz;
+        const bool dzl = (lg.dz0 && lv == 0) || (lg.dz1 && lv == lg.gnz);
 #pragma unroll
         for (int r = 1; r <= NY; ++r) {
-          const T g0 = (G[r][0] + G[r][2]) + (G[r - 1][0] - G[r - 1][2]);
-          const T g1 = (G[r][1] + G[r][3]) + (G[r - 1][1] - G[r - 1][3]);
-          const T nl = g0 + g1, nr = g0 - g1;
+          // (g0, g1) = (G_0 + G_2, G_1 + G_3) of row r + (G_0 - G_2, G_1 - G_3) of row r-1
+          const T2 g = V::add(V::add(G[r][0], G[r][1]), V::fma(G[r - 1][1], M1, G[r - 1][0]));
+          const T nl = g.x + g.y, nr = g.x - g.y;
           const T from_left = __shfl_up_sync(FULL, nr, 1, SX);
-          if (out_lane && lvin && ((rin >> r) & 1u)) {
-            const bool dir = ((rdxy >> r) & 1u) || dzl;
-            out(nbase + r * px + lv * pxy, dir, nl + from_left, vprev[r - 1]);
+          if (lg.out_lane && lvin && ((lg.rin >> r) & 1u)) {
+            const bool dir = ((lg.rdxy >> r) & 1u) || dzl;
+            out(lg.nbase + r * lg.px + lv * lg.pxy, dir, nl + from_left, vprev[r - 1]);
           }
         }
       }
@@ -153,8 +338,20 @@ __device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, cons
 #pragma unroll
     for (int r = 0; r < NF; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Fp[r][q] = F[r][q];
+      for (int h = 0; h < 2; ++h) Fp[r][h] = F[r][h];
   }
+}
+
+// The register-prefetch form with functor loads (see RegSrc).
+template <class T, int SX, int NY, class Coef, class Fetch, class Value, class Out>
+__device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, const Coef* __restrict__ coef, bool active,
+                                             int i0, int j0, int k0, int tzl, T sa, T sb, bool mask, Fetch&& fetch,
+                                             Value&& value, Out&& out) {
+  const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, i0, j0, mask);
+  using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
+  RegSrc<T, NY, CoefT, typename std::remove_reference<Fetch>::type, typename std::remove_reference<Value>::type> src(
+      coef, fetch, value, k0);
+  warp_tile_march<T, SX, NY>(lg, s, src, tzl, sa, sb, out);
 }
 
 }  // namespace heat

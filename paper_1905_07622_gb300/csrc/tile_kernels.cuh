@@ -458,14 +458,18 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
 
 // Warp-segment version of k_apply_dot (op_warp.cuh): a work item is a group
 // of SPC consecutive segment tiles of one simulation; the level loop has no
-// block barrier. Same results contract as k_apply_dot.
-template <class T, int SX, int NY, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_apply_dot_w(const SimDev* __restrict__ sims,
+// block barrier. Same results contract as k_apply_dot. STAGES = 0 loads one
+// level ahead into registers; STAGES >= 2 stages each thread's loads through
+// its own cp.async ring of that many levels in dynamic shared memory
+// (async_stage_bytes per thread). MINB blocks per SM bound the registers.
+template <class T, int SX, int NY, int WARPS, int STAGES, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* __restrict__ sims,
                                                             const int2* __restrict__ work,
                                                             const int* __restrict__ nwork_p) {
   constexpr int SPC = WARPS * (32 / SX);  // segments per block
   __shared__ double red[32];
   __shared__ ItemCache cache;
+  extern __shared__ __align__(16) unsigned char stage_smem[];
   int cur = -1;
   bool dep = false;
   allow_next_launch();
@@ -488,20 +492,28 @@ __global__ void __launch_bounds__(32 * WARPS) k_apply_dot_w(const SimDev* __rest
     const bool rs = c.restart != 0;
     const T beta = rs ? T(0) : (T)c.beta;
     T acc = T(0);
-    warp_tile_op<T, SX, NY>(
-        g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
-        (T)s.theta, true,
-        [&](int m, bool live) -> DirRaw<T> {
-          if (!live) return {T(0), T(0), T(0)};
-          return {pinv[m], r[m], rs ? T(0) : dold[m]};
-        },
-        [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; },
-        [&](int m, bool dir, T y, T v) {
-          const T qv = dir ? T(0) : y;
-          q[m] = qv;
-          dnew[m] = v;
-          acc += v * qv;
-        });
+    auto out = [&](int m, bool dir, T y, T v) {
+      const T qv = dir ? T(0) : y;
+      q[m] = qv;
+      dnew[m] = v;
+      acc += v * qv;
+    };
+    if constexpr (STAGES == 0) {
+      warp_tile_op<T, SX, NY>(
+          g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
+          (T)s.theta, true,
+          [&](int m, bool live) -> DirRaw<T> {
+            if (!live) return {T(0), T(0), T(0)};
+            return {pinv[m], r[m], rs ? T(0) : dold[m]};
+          },
+          [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
+    } else {
+      using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(IterVecs<T>::coef(s)[0])>::type>::type;
+      const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true);
+      AsyncSrc<T, NY, STAGES, CoefT> src(pinv, r, rs ? nullptr : dold, IterVecs<T>::coef(s), beta, stage_smem,
+                                         (int)blockDim.x, (int)threadIdx.x, tz * s.w_tz);
+      warp_tile_march<T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
+    }
     const T accv[1] = {acc};
     double tot[1];
     if (finish_item<T, 1>(s, wi.y, s.w_items, accv, tot, red)) {

@@ -70,7 +70,10 @@ def test_every_variant_and_segment_size_matches_oracle(precision, tol):
 def test_batch_bitwise_equal_to_alone_under_a_tuned_table():
     import paper_1905_07622_gb300 as hg
     n = hg.heat_tuning_num_variants()
-    hg.heat_tuning_set([n - 1, n - 1, 0], [256, 1024, 512])
+    info = [hg.heat_tuning_variant(v) for v in range(n)]
+    v64 = max(v for v in range(n) if info[v]["has_fp64"])
+    v32 = next((v for v in range(n) if info[v]["stages"] > 0), n - 1)  # a cp.async-staged kernel if any
+    hg.heat_tuning_set([v64, v32, 0], [256, 1024, 512])
     ps = [_problem(), W.random_box(9, 30, 5, seed=22, flux={0: 1.0}, nsteps=2, rtol=1e-11),
           W.lognormal_cube(1, n=24, nsteps=2)]
     for precision in ("fp64", "fp32_refined"):

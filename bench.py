@@ -258,13 +258,13 @@ def run_reference(args, world, rank):
 
 # ---------------------------------------------------------------- batch / serving
 
-def autotune(hg, p, precision, stream, flush, reps=20):
+def autotune(hg, p, precision, stream, reps=40):
     """Tune the kernel table for this problem's size bucket and precision
-    (untimed; one step first so the solver vectors hold a real iteration)."""
+    (untimed; CG iterations through the tick graph, as the solve runs them)."""
     with hg.Simulation.from_problem(p, precision=precision, stream=stream.cuda_stream) as s:
         s.step(1)
-        table, ms = hg.heat_autotune(s.sim, reps, flush)
-    return {"table": table, "best_ms_apply": ms}
+        table, ms = hg.heat_autotune(s.sim, reps)
+    return {"table": table, "best_ms_per_cg_iteration": ms}
 
 
 def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
@@ -273,14 +273,14 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
     import workloads as W
     ps = [W.lognormal_cube(s, n=40, nsteps=nsteps) for s in range(nsims)]
     tuning = None
-    if tune:
-        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-        tuning = autotune(hg, W.lognormal_cube(0, n=40, nsteps=2), "fp32_refined", stream, flush)
-        del flush
     sims = [hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream) for p in ps]
     b = hg.heat_batch_create([s.sim for s in sims], stream.cuda_stream)
     try:
         rc, _ = hg.heat_batch_step(b, 2, nsims)  # warm-up steps (graph capture, caches)
+        if tune:  # the whole batch's CG iterations through its tick graph (untimed)
+            table, ms = hg.heat_batch_autotune(b, 40)
+            tuning = {"table": table, "best_ms_per_cg_iteration": ms}
+            rc, _ = hg.heat_batch_step(b, 1, nsims)
         for s, p in zip(sims, ps):
             hg.heat_set_state(s.sim, p.u0, s.n_nodes)
         torch.cuda.synchronize()
@@ -385,7 +385,7 @@ def main():
         return
     p = W.inclusions_cube(nsteps=args.nsteps)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream, flush)
+    tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream)
     sim = hg.Simulation.from_problem(p, precision=args.precision, stream=stream.cuda_stream)
     nn, ne = sim.n_nodes, sim.n_elems
     rc_d = torch.tensor(p.rho_c, device="cuda")

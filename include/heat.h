@@ -278,7 +278,8 @@ heat_status heat_apply_dot_noalloc(int nx, int ny, int nz, const double extent[3
 
 /* Time `reps` CG iterations of the sim's current precision (the two tile
  * kernels of one iteration of Algorithm 1: apply+direction+dot, then
- * update+dot) with CUDA events recorded on the sim's stream around each
+ * update+dot; or the one fused kernel, reported as the apply with
+ * ms_update = 0) with CUDA events recorded on the sim's stream around each
  * launch. If flush != NULL, flush_bytes of it are overwritten before every
  * timed launch (to evict L2). Outputs the mean ms per launch of each kernel
  * and their algorithmic DRAM bytes per launch (vectors and coefficients each
@@ -314,25 +315,36 @@ typedef struct heat_tuning {
 int heat_tuning_num_variants(void);
 /* Shape of variant v: segment width in nodes along x (one lane per node),
  * node rows along y per lane, warps per block, whether an FP64 kernel exists,
- * and how its loads travel: 0 = plain loads one level ahead into registers,
+ * how its loads travel (0 = plain loads one level ahead into registers,
  * S >= 2 = each thread's own cp.async copies S-1 levels ahead into an S-stage
- * ring in shared memory. Any output may be NULL. HEAT_ERR_ARG for an unknown v. */
-heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64, int* stages);
+ * ring in shared memory), and whether it is a fused iteration (FP32 paths
+ * only: one kernel per CG iteration in the Chronopoulos-Gear arrangement of
+ * PCG, which forms both inner products of an iteration in one reduction,
+ * instead of an apply kernel and an update kernel). Any output may be NULL.
+ * HEAT_ERR_ARG for an unknown v. */
+heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64, int* stages,
+                                int* fused);
 heat_status heat_tuning_get(heat_tuning* t);
 /* HEAT_ERR_ARG (table unchanged) for an unknown variant, a variant without
  * an FP64 kernel in variant[HEAT_FP64], or a segment size out of range. */
 heat_status heat_tuning_set(const heat_tuning* t);
-/* Time the apply kernel of one CG iteration (as heat_profile_iteration, `reps`
- * launches after 3 warm-up launches, flush as there) for every candidate
- * (block tile; each variant with a segment size of 256, 512, 1024 or 2048
- * nodes) on this simulation's mesh and precision, and store the fastest in
- * the table entries of that precision and of the mesh's size bucket. Outputs
- * the resulting table and the winner's mean ms per launch (either may be
- * NULL). Needs a prior heat_step; leaves the simulation's solver state
+/* Time CG iterations of this simulation as a solve runs them (the captured
+ * tick graph of its engine, about `reps` iterations after 8 warm-up ones,
+ * every iteration on a seeded residual that does not converge) for every
+ * candidate (block tile; each variant with a segment size of 256, 512, 1024
+ * or 2048 nodes) on this simulation's mesh and precision, and store the
+ * fastest in the table entries of that precision and of the mesh's size
+ * bucket. Outputs the resulting table and the winner's mean ms per iteration
+ * (either may be NULL). Needs a prior heat_step; leaves the simulation's solver state
  * undefined (call heat_set_state or heat_set_history before stepping again);
  * its next heat_step builds its engine under the new table. */
-heat_status heat_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, heat_tuning* best,
-                          double* best_ms);
+heat_status heat_autotune(heat_sim* sim, int reps, heat_tuning* best, double* best_ms);
+/* The same over all members of a batch at once (every candidate's launches
+ * carry all of them; the segment size is stored for the first member's size
+ * bucket); needs a prior heat_batch_step, leaves the members' solver state
+ * undefined and rebuilds the batch's engine under the new table. A failure
+ * to rebuild leaves the batch unusable (destroy it). */
+heat_status heat_batch_autotune(heat_batch* batch, int reps, heat_tuning* best, double* best_ms);
 
 const char* heat_last_error(void);
 const char* heat_status_string(heat_status s);

@@ -124,10 +124,11 @@ _SIGS = [
                                          _VP, _VP, _VP, _VP, _VP]),
     ("heat_tuning_num_variants", C.c_int, []),
     ("heat_tuning_variant", C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("heat_tuning_get", C.c_int, [C.POINTER(heat_tuning)]),
     ("heat_tuning_set", C.c_int, [C.POINTER(heat_tuning)]),
-    ("heat_autotune", C.c_int, [_VP, C.c_int, _VP, C.c_size_t, C.POINTER(heat_tuning), _DP]),
+    ("heat_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
+    ("heat_batch_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
     ("heat_last_error", C.c_char_p, []),
     ("heat_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -463,9 +464,10 @@ def heat_tuning_num_variants() -> int:
 
 def heat_tuning_variant(v: int) -> dict:
     load_library()
-    a, b, c, d, e = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
-    _check(_lib.heat_tuning_variant(int(v), C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e)))
-    return {"seg_width": a.value, "rows": b.value, "warps": c.value, "has_fp64": bool(d.value), "stages": e.value}
+    a, b, c, d, e, f = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.heat_tuning_variant(int(v), C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)))
+    return {"seg_width": a.value, "rows": b.value, "warps": c.value, "has_fp64": bool(d.value), "stages": e.value,
+            "fused": bool(f.value)}
 
 
 def heat_tuning_get() -> dict:
@@ -481,13 +483,19 @@ def heat_tuning_set(variant, seg_nodes):
     _check(_lib.heat_tuning_set(C.byref(t)))
 
 
-def heat_autotune(sim, reps: int, flush=None):
-    """Tune the table for this sim's precision and size; returns (table, best ms per apply)."""
+def heat_autotune(sim, reps: int):
+    """Tune the table for this sim's precision and size; returns (table, best ms per CG iteration)."""
     t = heat_tuning()
     ms = C.c_double()
-    fp = C.c_void_p(_dev_ptr(flush)) if flush is not None else C.c_void_p(0)
-    fb = flush.numel() * flush.element_size() if flush is not None else 0
-    _check(_lib.heat_autotune(sim, int(reps), fp, fb, C.byref(t), C.byref(ms)))
+    _check(_lib.heat_autotune(sim, int(reps), C.byref(t), C.byref(ms)))
+    return t.as_dict(), ms.value
+
+
+def heat_batch_autotune(batch, reps: int):
+    """heat_autotune over every member of a batch; returns (table, best ms per CG iteration)."""
+    t = heat_tuning()
+    ms = C.c_double()
+    _check(_lib.heat_batch_autotune(batch, int(reps), C.byref(t), C.byref(ms)))
     return t.as_dict(), ms.value
 
 

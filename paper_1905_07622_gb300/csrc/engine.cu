@@ -30,13 +30,14 @@ struct KernelSet {
   int pw_chunk;  // nodes per pointwise (k_update) work item
   int seg_nodes[3];  // warp-segment tile size per mesh-size bucket
   int apply_w_smem;  // dynamic shared memory of apply_w per block
+  bool fused;        // apply_w is k_cg_iter: one kernel per CG iteration, no update kernel
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
   return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0,
-          pw_chunk<T>(), {512, 512, 512}, 0};
+          pw_chunk<T>(), {512, 512, 512}, 0, false};
 }
 
 // Warp-segment apply variants the tuner chooses from: segment width, rows per
@@ -46,6 +47,7 @@ struct WVariant {
   int sx, ny, warps, stages;
   TileFn f32, f64;
   int smem32, smem64;  // dynamic shared memory per block
+  bool fused;          // FP32 only: the fused iteration kernel k_cg_iter
 };
 template <class T, int SX, int NY, int W, int S, int MINB, bool ON>
 static constexpr TileFn wfn() {
@@ -56,14 +58,19 @@ template <int SX, int NY, int W, int S, int MINB, int MINB64>
 static constexpr WVariant wv() {
   return {SX, NY, W, S, wfn<float, SX, NY, W, S, MINB, true>(), wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0)>(),
           S ? 32 * W * async_stage_bytes<float, NY, (S ? S : 2)>() : 0,
-          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0};
+          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0, false};
+}
+template <int SX, int NY, int W, int MINB>
+static constexpr WVariant wv_fused() {
+  return {SX, NY, W, 0, k_cg_iter<SX, NY, W, MINB>, nullptr, 0, 0, true};
 }
 // (segment width, rows, warps, stages, min blocks per SM for float / double,
 // 0 = no double kernel)
 static const WVariant kVariants[] = {
     wv<16, 4, 4, 0, 3, 0>(), wv<32, 4, 4, 0, 3, 0>(), wv<16, 2, 8, 0, 2, 1>(), wv<32, 2, 4, 0, 4, 1>(),
     wv<16, 4, 4, 3, 4, 0>(), wv<32, 4, 4, 3, 4, 0>(), wv<16, 2, 8, 3, 2, 1>(), wv<32, 4, 4, 3, 3, 0>(),
-    wv<32, 4, 4, 4, 3, 0>(),
+    wv<32, 4, 4, 4, 3, 0>(),     wv_fused<16, 4, 4, 2>(), wv_fused<32, 4, 4, 2>(), wv_fused<16, 4, 4, 3>(),
+    wv_fused<32, 4, 4, 3>(),     wv_fused<16, 2, 8, 2>(), wv_fused<32, 2, 4, 4>(),
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -76,13 +83,14 @@ static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }
 
-bool variant_info(int v, int info[5]) {
+bool variant_info(int v, int info[6]) {
   if (v < 0 || v >= kNumVariants) return false;
   info[0] = kVariants[v].sx;
   info[1] = kVariants[v].ny;
   info[2] = kVariants[v].warps;
   info[3] = kVariants[v].f64 != nullptr;
   info[4] = kVariants[v].stages;
+  info[5] = kVariants[v].fused;
   return true;
 }
 
@@ -120,6 +128,7 @@ static KernelSet kernel_set(int prec, const Tuning& t) {
       k.wny = v.ny;
       k.wwarps = v.warps;
       k.apply_w_smem = prec == P_FP64 ? v.smem64 : v.smem32;
+      k.fused = v.fused;
       if (k.apply_w_smem > 0)
         cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
     }
@@ -174,6 +183,9 @@ struct Engine {
   std::vector<int2> h_op, h_pw;
 };
 
+// Kernels in one tick: k_open, then per iteration apply + update, or the fused kernel.
+static int tick_launches(const Engine* e) { return 1 + (e->ks.fused ? 1 : 2) * e->iters_per_tick; }
+
 // Operator tile geometry of one simulation: (SX-1) x (SY-1) node columns per
 // tile, tz_len levels. tz_len trades z-halo work (3 extra levels per tile)
 // against the number of tiles. It depends on the simulation's own mesh only
@@ -225,6 +237,7 @@ static heat_status engine_upload(Engine* e) {
   for (size_t i = 0; i < e->sims.size(); ++i) {
     SimDev d = e->sims[i]->dev;
     tile_geometry(d, e->ks);
+    d.fused = e->ks.fused ? 1 : 0;
     d.partial = e->d_partial + 4 * item_base;
     item_base += std::max(std::max(d.ntiles, d.npw), d.w_items);
     for (int t = 0; t < d.ntiles; ++t) e->h_op.push_back(make_int2((int)i, t));
@@ -317,7 +330,7 @@ static heat_status engine_capture(Engine* e) {
     cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
     for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
       lerr = launch(afn, agrid, athreads, awork, anwork, asmem);
-      if (lerr == cudaSuccess)
+      if (lerr == cudaSuccess && !e->ks.fused)
         lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1, 0);
     }
     err = cudaStreamEndCapture(cap, &e->graph);
@@ -450,7 +463,7 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
   for (;;) {
     for (int t = 0; t < ticks_per_poll; ++t) CUDA_TRY(cudaGraphLaunch(e->gexec, e->stream));
     ticks += ticks_per_poll;
-    e->launches += (long long)ticks_per_poll * (1 + 2 * e->iters_per_tick) + 1;
+    e->launches += (long long)ticks_per_poll * tick_launches(e) + 1;
     k_count_unfinished<<<1, 256, 0, e->stream>>>(e->d_sims, (int)e->sims.size(), e->d_unfinished);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(e->h_unfinished, e->d_unfinished, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
@@ -492,7 +505,7 @@ __global__ void k_gather_phases(const SimDev* __restrict__ sims, int nsims, int*
 
 heat_status engine_launch_ticks(Engine* e, int nticks) {
   for (int t = 0; t < nticks; ++t) CUDA_TRY(cudaGraphLaunch(e->gexec, e->stream));
-  e->launches += (long long)nticks * (1 + 2 * e->iters_per_tick);
+  e->launches += (long long)nticks * tick_launches(e);
   return HEAT_OK;
 }
 
@@ -567,6 +580,60 @@ __global__ void k_profile_seed(T* __restrict__ r, const T* __restrict__ pinv, lo
   if ((threadIdx.x & 31) == 0) atomicAdd(delta, acc);
 }
 
+// Puts every member into the middle of an inner solve that cannot converge:
+// a seeded, well-scaled residual (pseudo-random entries in [-1, 1)) with
+// delta = r^T P^-1 r computed for it, phase ITER, restart. Timed iterations
+// are then ordinary CG iterations whatever state the members were left in
+// (a converged step leaves a residual near underflow).
+static heat_status profile_arm(Engine* e, double* d_delta, std::vector<double>& h_delta) {
+  heat_status st = HEAT_OK;
+  if (cudaMemsetAsync(d_delta, 0, sizeof(double) * e->sims.size(), e->stream) != cudaSuccess)
+    return set_error(HEAT_ERR_CUDA, "profile: memset failed");
+  for (size_t i = 0; i < e->sims.size(); ++i) {
+    heat_sim* s = e->sims[i];
+    const int g = (int)std::min<long long>((s->nn + 255) / 256, 4LL * sm_count());
+    if (e->prec == P_FP64) {
+      k_profile_seed<double><<<g, 256, 0, e->stream>>>(s->dev.r, s->dev.pinv, s->nn, d_delta + i);
+    } else {
+      st = sim_read_scalars(s);
+      if (st != HEAT_OK) return st;
+      const int slot = e->ks.fused ? (s->h_sc->cgs & 1) : 0;
+      k_profile_seed<float><<<g, 256, 0, e->stream>>>(s->dev.rc32[slot], s->dev.pinv32, s->nn, d_delta + i);
+    }
+  }
+  if (cudaMemcpyAsync(h_delta.data(), d_delta, sizeof(double) * e->sims.size(), cudaMemcpyDeviceToHost,
+                      e->stream) != cudaSuccess ||
+      cudaStreamSynchronize(e->stream) != cudaSuccess)
+    return set_error(HEAT_ERR_CUDA, "profile: residual seeding failed");
+  for (size_t i = 0; i < e->sims.size(); ++i) {
+    heat_sim* s = e->sims[i];
+    st = sim_read_scalars(s);
+    if (st != HEAT_OK) return st;
+    SimScalars* sc = s->h_sc;
+    sc->phase = PH_ITER;
+    sc->iter = 1;
+    sc->iter_step = 0;
+    sc->restart = 1;
+    sc->thresh = -1.0;
+    sc->thresh_in = -1.0;
+    sc->count = 0;
+    sc->delta = h_delta[i] > 0.0 ? h_delta[i] : 1.0;
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) return st;
+  }
+  return HEAT_OK;
+}
+
+static heat_status profile_check(Engine* e) {
+  for (heat_sim* s : e->sims) {
+    heat_status st = sim_read_scalars(s);
+    if (st != HEAT_OK) return st;
+    if (s->h_sc->phase != PH_ITER)
+      return set_error(HEAT_ERR_BREAKDOWN, "profile: the iteration left PH_ITER (status %d)", s->h_sc->status);
+  }
+  return HEAT_OK;
+}
+
 heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes, double* ms_apply,
                            double* ms_update, double* bytes_apply, double* bytes_update) {
   const int chunk = 40;  // below the inner-solve cap and the true-residual period
@@ -574,10 +641,6 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   for (int i = 0; i < 4 * chunk; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
   double ta = 0.0, tu = 0.0;
   heat_status st = HEAT_OK;
-  // Every chunk restarts each member from the same well-scaled residual
-  // (pseudo-random entries in [-1, 1)) with delta = r^T P^-1 r computed for
-  // it, so the timed iterations are ordinary CG iterations whatever state the
-  // members were left in (a converged step leaves a residual near underflow).
   double* d_delta = nullptr;
   std::vector<double> h_delta(e->sims.size(), 0.0);
   if (cudaMalloc(&d_delta, sizeof(double) * e->sims.size()) != cudaSuccess) {
@@ -586,37 +649,7 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   }
   for (int done = 0; done < reps && st == HEAT_OK;) {
     const int c = std::min(reps - done, chunk);
-    if (cudaMemsetAsync(d_delta, 0, sizeof(double) * e->sims.size(), e->stream) != cudaSuccess)
-      st = set_error(HEAT_ERR_CUDA, "profile: memset failed");
-    for (size_t i = 0; i < e->sims.size() && st == HEAT_OK; ++i) {
-      const heat_sim* s = e->sims[i];
-      const int g = (int)std::min<long long>((s->nn + 255) / 256, 4LL * sm_count());
-      if (e->prec == P_FP64)
-        k_profile_seed<double><<<g, 256, 0, e->stream>>>(s->dev.r, s->dev.pinv, s->nn, d_delta + i);
-      else
-        k_profile_seed<float><<<g, 256, 0, e->stream>>>(s->dev.r32, s->dev.pinv32, s->nn, d_delta + i);
-    }
-    if (st == HEAT_OK &&
-        (cudaMemcpyAsync(h_delta.data(), d_delta, sizeof(double) * e->sims.size(), cudaMemcpyDeviceToHost,
-                         e->stream) != cudaSuccess ||
-         cudaStreamSynchronize(e->stream) != cudaSuccess))
-      st = set_error(HEAT_ERR_CUDA, "profile: residual seeding failed");
-    for (size_t i = 0; i < e->sims.size() && st == HEAT_OK; ++i) {  // every member iterates, none converges
-      heat_sim* s = e->sims[i];
-      st = sim_read_scalars(s);
-      if (st != HEAT_OK) break;
-      SimScalars* sc = s->h_sc;
-      sc->phase = PH_ITER;
-      sc->iter = 1;
-      sc->iter_step = 0;
-      sc->restart = 1;
-      sc->thresh = -1.0;
-      sc->thresh_in = -1.0;
-      sc->count = 0;
-      sc->delta = h_delta[i] > 0.0 ? h_delta[i] : 1.0;
-      st = sim_write_scalars(s);
-      if (st != HEAT_OK) break;
-    }
+    st = profile_arm(e, d_delta, h_delta);
     if (st != HEAT_OK) break;
     for (int i = 0; i < c; ++i) {
       if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
@@ -630,9 +663,9 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
         afn<<<agrid, athreads, asmem, e->stream>>>(e->d_sims, awork, anwork);
       }
       cudaEventRecord(ev[4 * i + 1], e->stream);
-      if (flush) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
+      if (flush && !e->ks.fused) k_flush_read<<<sm_count() * 4, 256, 0, e->stream>>>((const uint4*)flush, flush_bytes / 16, (unsigned int*)e->d_unfinished);
       cudaEventRecord(ev[4 * i + 2], e->stream);
-      e->ks.update<<<e->grid_pw, kPwThreads, 0, e->stream>>>(e->d_sims, e->d_work_pw, e->d_nwork + 1);
+      if (!e->ks.fused) e->ks.update<<<e->grid_pw, kPwThreads, 0, e->stream>>>(e->d_sims, e->d_work_pw, e->d_nwork + 1);
       cudaEventRecord(ev[4 * i + 3], e->stream);
     }
     if (cudaStreamSynchronize(e->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -642,16 +675,11 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
     for (int i = 0; i < c; ++i) {
       float a = 0.f, u = 0.f;
       cudaEventElapsedTime(&a, ev[4 * i + 0], ev[4 * i + 1]);
-      cudaEventElapsedTime(&u, ev[4 * i + 2], ev[4 * i + 3]);
+      if (!e->ks.fused) cudaEventElapsedTime(&u, ev[4 * i + 2], ev[4 * i + 3]);
       ta += a;
       tu += u;
     }
-    for (heat_sim* s : e->sims) {
-      if (st != HEAT_OK) break;
-      st = sim_read_scalars(s);
-      if (st == HEAT_OK && s->h_sc->phase != PH_ITER)
-        st = set_error(HEAT_ERR_BREAKDOWN, "profile: the iteration left PH_ITER (status %d)", s->h_sc->status);
-    }
+    st = profile_check(e);
     done += c;
   }
   for (int i = 0; i < 4 * chunk; ++i) cudaEventDestroy(ev[i]);
@@ -667,6 +695,8 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
     if (e->prec == P_FP64) {
       ba += n * (3 * 8 + 2 * 8) + ne * 16;    // r, P^-1, d_old in; d, q out; (rho_c, k)
       bu += n * (2 * 8 + 8 + 2 * 8 + 8 + 8);  // x in/out, d, r in/out, q, P^-1
+    } else if (e->ks.fused) {
+      ba += n * (6 * 4 + 5 * 4) + ne * 8;  // r, w, s, P^-1, p, e in; r', s', w', p, e out; (rho_c, k)
     } else {
       ba += n * (3 * 4 + 2 * 4) + ne * 8;
       bu += n * (2 * 4 + 4 + 2 * 4 + 4 + 4);
@@ -677,11 +707,53 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   return HEAT_OK;
 }
 
-heat_status engine_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, int* best_variant, int* best_seg,
+heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
+  const int chunk_ticks = std::max(1, 40 / e->iters_per_tick);  // below the inner cap
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return set_error(HEAT_ERR_CUDA, "timing: event creation failed");
+  }
+  heat_status st = HEAT_OK;
+  double* d_delta = nullptr;
+  std::vector<double> h_delta(e->sims.size(), 0.0);
+  if (cudaMalloc(&d_delta, sizeof(double) * e->sims.size()) != cudaSuccess) {
+    cudaGetLastError();
+    st = set_error(HEAT_ERR_NOMEM, "timing: no room for the residual norms");
+  }
+  double ms = 0.0;
+  long long iters = 0;
+  for (int done = 0; done < reps && st == HEAT_OK;) {
+    const int ticks = std::min(chunk_ticks, std::max(1, (reps - done + e->iters_per_tick - 1) / e->iters_per_tick));
+    st = profile_arm(e, d_delta, h_delta);
+    if (st != HEAT_OK) break;
+    cudaEventRecord(a, e->stream);
+    for (int t = 0; t < ticks && st == HEAT_OK; ++t)
+      if (cudaGraphLaunch(e->gexec, e->stream) != cudaSuccess) st = set_error(HEAT_ERR_CUDA, "timing: graph launch failed");
+    cudaEventRecord(b, e->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) st = set_error(HEAT_ERR_CUDA, "timing: synchronisation failed");
+    if (st != HEAT_OK) break;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    ms += t;
+    iters += (long long)ticks * e->iters_per_tick;
+    done += ticks * e->iters_per_tick;
+    st = profile_check(e);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(d_delta);
+  if (st != HEAT_OK) return st;
+  *ms_per_iter = ms / (double)std::max(1LL, iters);
+  return HEAT_OK;
+}
+
+heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* best_variant, int* best_seg,
                             double* best_ms) {
   static const int kSegs[] = {256, 512, 1024, 2048};
-  const int prec = sim->prm.precision;
-  const int bucket = size_bucket(sim->nn);
+  const int prec = sims[0]->prm.precision;
+  const int bucket = size_bucket(sims[0]->nn);
   const Tuning base = tuning_get();
   Tuning best = base;
   double best_t = 1e300;
@@ -693,14 +765,15 @@ heat_status engine_autotune(heat_sim* sim, int reps, void* flush, size_t flush_b
       t.variant[prec] = v;
       if (v >= 0) t.seg_nodes[bucket] = kSegs[si];
       Engine* e = nullptr;
-      st = engine_create(&sim, 1, prec, sim->stream, &e, &t);
+      st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
       if (st != HEAT_OK) break;
-      double ma = 0.0, mu = 0.0, ba = 0.0, bu = 0.0;
-      st = engine_profile(e, 3, flush, flush_bytes, &ma, &mu, &ba, &bu);  // warm-up
-      if (st == HEAT_OK) st = engine_profile(e, reps, flush, flush_bytes, &ma, &mu, &ba, &bu);
+      // CG iterations as the solve runs them: the captured tick graph
+      double ms = 0.0;
+      st = engine_time_iterations(e, 8, &ms);  // warm-up
+      if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
       engine_destroy(e);
-      if (st == HEAT_OK && ma < best_t) {
-        best_t = ma;
+      if (st == HEAT_OK && ms < best_t) {
+        best_t = ms;
         best = t;
       }
     }

@@ -60,14 +60,21 @@ struct Tuning {
 };
 int size_bucket(long long nn);
 int num_variants();
-// {segment width, rows per thread, warps per block, has an FP64 kernel, cp.async stages}
-bool variant_info(int v, int info[5]);
+// {segment width, rows per thread, warps per block, has an FP64 kernel, cp.async stages,
+//  fused iteration kernel}
+bool variant_info(int v, int info[6]);
 Tuning tuning_get();
 heat_status tuning_set(const Tuning& t);
-// Time the apply kernel of every candidate (variant, segment size) on `sim`
-// (which must have run a step) and store the fastest in the table.
-heat_status engine_autotune(heat_sim* sim, int reps, void* flush, size_t flush_bytes, int* best_variant, int* best_seg,
+// Time CG iterations through the tick graph (engine_time_iterations) for
+// every candidate (variant, segment size) on the simulations together (each
+// must have run a step) and store the fastest in the table entries of their
+// precision and of the first one's size bucket.
+heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* best_variant, int* best_seg,
                             double* best_ms);
+// Mean ms per CG iteration over about `reps` iterations run through the
+// engine's captured tick graph (as a solve runs them), every member kept
+// iterating; leaves the members' solver state undefined.
+heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter);
 
 // A set of simulations driven together by one captured tick graph (kernel
 // choice from the tuning table, or from `tun` when given).

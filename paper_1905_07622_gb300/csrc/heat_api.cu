@@ -56,7 +56,7 @@ extern "C" void heat_params_default(heat_params* p) {
   p->resid_period = 50;
   p->poll_period = 32;
   p->precision = HEAT_FP64;
-  p->inner_rtol = 1e-4;
+  p->inner_rtol = 1e-5;
   p->max_outer = 40;
 }
 
@@ -293,6 +293,13 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   ALLOC(d.d32[0], N4, float*);
   ALLOC(d.d32[1], N4, float*);
   ALLOC(d.pinv32, N4, float*);
+  ALLOC(d.rc32[1], N4, float*);
+  ALLOC(d.wc32[1], N4, float*);
+  ALLOC(d.p32, N4, float*);
+  d.rc32[0] = d.r32;
+  d.wc32[0] = d.q32;
+  d.sc32[0] = d.d32[0];
+  d.sc32[1] = d.d32[1];
   s->iters_log_cap = 4096;
   ALLOC(d.iters_log, sizeof(int) * s->iters_log_cap, int*);
   d.iters_log_len = s->iters_log_cap;
@@ -320,6 +327,9 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
         cudaMemsetAsync(d.d32[0], 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.d32[1], 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.e32, 0, N4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d.p32, 0, N4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d.rc32[1], 0, N4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d.wc32[1], 0, N4, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->d_q6, b.flux, sizeof(double) * 6, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
       st = set_error(HEAT_ERR_CUDA, "heat_sim_create: initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
       goto fail;
@@ -503,8 +513,8 @@ heat_status heat::sim_prepare_steps(heat_sim* s, int nsteps) {
 }
 
 size_t heat::sim_footprint(long long nn, long long ne) {
-  // 12 FP64 and 6 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
-  return (size_t)nn * (12 * 8 + 6 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
+  // 12 FP64 and 9 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
+  return (size_t)nn * (12 * 8 + 9 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
          4096 * sizeof(int) + 1024;
 }
 
@@ -677,14 +687,15 @@ extern "C" heat_status heat_profile_iteration(heat_sim* s, int reps, void* flush
 extern "C" int heat_tuning_num_variants(void) { return num_variants(); }
 
 extern "C" heat_status heat_tuning_variant(int v, int* seg_width, int* rows, int* warps, int* has_fp64,
-                                           int* stages) {
-  int info[5];
+                                           int* stages, int* fused) {
+  int info[6];
   if (!variant_info(v, info)) return set_error(HEAT_ERR_ARG, "heat_tuning_variant: unknown variant %d", v);
   if (seg_width) *seg_width = info[0];
   if (rows) *rows = info[1];
   if (warps) *warps = info[2];
   if (has_fp64) *has_fp64 = info[3];
   if (stages) *stages = info[4];
+  if (fused) *fused = info[5];
   return HEAT_OK;
 }
 
@@ -708,16 +719,31 @@ extern "C" heat_status heat_tuning_set(const heat_tuning* t) {
   return tuning_set(x);
 }
 
-extern "C" heat_status heat_autotune(heat_sim* s, int reps, void* flush, size_t flush_bytes, heat_tuning* best,
-                                     double* best_ms) {
+extern "C" heat_status heat_autotune(heat_sim* s, int reps, heat_tuning* best, double* best_ms) {
   if (!s || reps < 1) return set_error(HEAT_ERR_ARG, "heat_autotune: bad argument");
   if (!s->eng) return set_error(HEAT_ERR_ARG, "heat_autotune: call heat_step first");
   int v = 0, seg = 0;
   double ms = 0.0;
-  heat_status st = engine_autotune(s, reps, flush, flush_bytes, &v, &seg, &ms);
+  heat_status st = engine_autotune(&s, 1, reps, &v, &seg, &ms);
   if (st != HEAT_OK) return st;
   engine_destroy(s->eng);  // rebuilt under the new table by the next heat_step
   s->eng = nullptr;
+  if (best) st = heat_tuning_get(best);
+  if (best_ms) *best_ms = ms;
+  return st;
+}
+
+extern "C" heat_status heat_batch_autotune(heat_batch* b, int reps, heat_tuning* best, double* best_ms) {
+  if (!b || reps < 1) return set_error(HEAT_ERR_ARG, "heat_batch_autotune: bad argument");
+  int v = 0, seg = 0;
+  double ms = 0.0;
+  heat_status st = engine_autotune(b->sims.data(), (int)b->sims.size(), reps, &v, &seg, &ms);
+  if (st != HEAT_OK) return st;
+  // rebuild the batch's engine under the new table
+  engine_destroy(b->eng);
+  b->eng = nullptr;
+  st = engine_create(b->sims.data(), (int)b->sims.size(), b->sims[0]->prm.precision, b->stream, &b->eng);
+  if (st != HEAT_OK) return st;
   if (best) st = heat_tuning_get(best);
   if (best_ms) *best_ms = ms;
   return st;

@@ -42,7 +42,7 @@ struct SimScalars {
   int id;          // current direction slot (0/1)
   int max_iters_step;
   unsigned int count;  // tiles finished in the running kernel
-  int pad_;
+  int cgs;             // FP32 fused iteration: current slot of r, w, s (0/1)
   double delta;    // r^T P^-1 r of the current solve
   double delta_b;  // b^T P^-1 b of the step
   double thresh;   // rtol^2 * delta_b
@@ -63,7 +63,8 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   // warp-segment tiles of the FP32 apply: (SX-2) x NY x w_tz nodes each
   int w_ntx, w_nty, w_ntz, w_tz, w_ntiles;
   int w_items;                // work items (groups of segment tiles per block)
-  int w_pad_[2];
+  int fused;                  // the engine runs the FP32 inner solve as one fused kernel per iteration
+  int w_pad_;
   long long nn;               // nodes
   uint32_t dir_faces;         // Dirichlet face bits
   int prec;                   // Prec
@@ -93,6 +94,13 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   float* e32;
   float* d32[2];
   float* pinv32;
+  // The fused FP32 iteration (one kernel per CG iteration, see k_cg_iter):
+  // r, w = A u and s = A p in two slots each (slot cgs is current), p.
+  // rc32[0] = r32, wc32[0] = q32, sc32 = d32.
+  float* rc32[2];
+  float* wc32[2];
+  float* sc32[2];
+  float* p32;
   double* partial;            // 2 per tile
   int* iters_log;             // CG iterations of each step
   int iters_log_len;

@@ -3,7 +3,10 @@
 Requests are submitted while others are running; each result must be bitwise
 identical to the same simulation stepped alone (its reductions do not depend
 on what shares the launches) and match the oracle within the refined path's
-1e-8 tolerance.
+1e-8 tolerance. The stopping rule bounds the preconditioned residual, and the
+field error can exceed it by up to the condition number, so the parity
+requests are solved to rtol 1e-10 (the serving workload's own 1e-8 is a
+residual tolerance, not a field one).
 """
 import time
 
@@ -27,7 +30,10 @@ def _alone(p, precision="fp32_refined"):
 
 
 def _requests():
-    return [W.serving_request(r, n_min=8, n_max=24) for r in range(6)]
+    ps = [W.serving_request(r, n_min=8, n_max=24) for r in range(6)]
+    for p in ps:
+        p.rtol = 1e-10
+    return ps
 
 
 def test_staggered_requests_equal_alone_and_oracle():

@@ -127,3 +127,31 @@ def test_autotune_picks_a_valid_entry_and_keeps_parity(precision):
     ref = pins.oracle_steps(p)
     err = np.linalg.norm(got - ref.u[2]) / np.linalg.norm(ref.u[2])
     assert err <= (1e-9 if precision == "fp64" else 1e-8), err
+
+
+def test_batch_autotune_rebuilds_and_keeps_parity():
+    import paper_1905_07622_gb300 as hg
+    ps = [W.lognormal_cube(s, n=16, nsteps=2) for s in range(3)]
+    for p in ps:
+        p.rtol = 1e-11
+    sims = [hg.Simulation.from_problem(p, precision="fp32_refined") for p in ps]
+    try:
+        b = hg.heat_batch_create([s.sim for s in sims])
+        try:
+            rc, _ = hg.heat_batch_step(b, 1, len(ps))
+            assert rc == 0
+            table, ms = hg.heat_batch_autotune(b, 8)
+            assert ms > 0.0 and table == hg.heat_tuning_get()
+            for s, p in zip(sims, ps):
+                hg.heat_set_history(s.sim, p.u0, None, 0, p.n_nodes)
+            rc, stats = hg.heat_batch_step(b, 2, len(ps))
+            assert rc == 0, hg.heat_last_error()
+            got = [s.state() for s in sims]
+        finally:
+            hg.heat_destroy_batch(b)
+    finally:
+        for s in sims:
+            s.close()
+    for g, p in zip(got, ps):
+        ref = pins.oracle_steps(p)
+        assert np.linalg.norm(g - ref.u[2]) <= 1e-8 * np.linalg.norm(ref.u[2])

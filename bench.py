@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning table")
+    ap.add_argument("--tuning-json", default="",
+                    help='set the kernel tuning table instead of autotuning, e.g. '
+                         '\'{"variant": [-1, 1, 0], "seg_nodes": [2048, 1024, 512]}\'')
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -267,7 +270,7 @@ def autotune(hg, p, precision, stream, reps=40):
     return {"table": table, "best_ms_per_cg_iteration": ms}
 
 
-def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
+def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tuning=False):
     """256 independent 40^3 samples with log-normal k (seeds 3000+s), FP32
     refined, one engine: every launch carries all samples."""
     import workloads as W
@@ -277,7 +280,7 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
     b = hg.heat_batch_create([s.sim for s in sims], stream.cuda_stream)
     try:
         rc, _ = hg.heat_batch_step(b, 2, nsims)  # warm-up steps (graph capture, caches)
-        if tune:  # the whole batch's CG iterations through its tick graph (untimed)
+        if tune and not fixed_tuning:  # the whole batch's CG iterations through its tick graph (untimed)
             table, ms = hg.heat_batch_autotune(b, 40)
             tuning = {"table": table, "best_ms_per_cg_iteration": ms}
             rc, _ = hg.heat_batch_step(b, 1, nsims)
@@ -297,7 +300,9 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True):
         dof = sims[0].n_nodes
         # the batch's CG-iteration kernels timed alone (L2 flushed before each launch)
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        torch.cuda.nvtx.range_push("roofline_batch")  # ncu captures filter on this range
         prof = hg.heat_batch_profile_iteration(b, 20, flush)
+        torch.cuda.nvtx.range_pop()
         peak, _ = measured_peaks()
         achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
         return {"workload": f"{nsims} x lognormal_cube_40 (68,921 DOF each), {nsteps} steps, dt=2e-3, theta=0.5, rtol 1e-10, fp32_refined",
@@ -380,12 +385,22 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.batch_only:  # the batched workload alone (used for profiling captures)
+        fixed = bool(args.tuning_json)
+        if fixed:
+            t = json.loads(args.tuning_json)
+            hg.heat_tuning_set(t["variant"], t["seg_nodes"])
         print(json.dumps({"batched": run_batch(hg, torch, args.batch_sims, args.batch_steps, stream,
-                                               not args.no_autotune)}), flush=True)
+                                               not args.no_autotune, fixed)}), flush=True)
         return
     p = W.inclusions_cube(nsteps=args.nsteps)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream)
+    fixed = bool(args.tuning_json)
+    if fixed:
+        t = json.loads(args.tuning_json)
+        hg.heat_tuning_set(t["variant"], t["seg_nodes"])
+        tuning = {"table": hg.heat_tuning_get(), "set_by": "--tuning-json"}
+    else:
+        tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream)
     sim = hg.Simulation.from_problem(p, precision=args.precision, stream=stream.cuda_stream)
     nn, ne = sim.n_nodes, sim.n_elems
     rc_d = torch.tensor(p.rho_c, device="cuda")
@@ -461,7 +476,9 @@ def main():
 
     # dominant kernel (apply + direction + d.q of the inner solve), timed alone
     # with CUDA events on this stream, L2 flushed before each launch
+    torch.cuda.nvtx.range_push("roofline")  # ncu captures filter on this range
     prof = hg.heat_profile_iteration(sim.sim, args.profile_reps, flush)
+    torch.cuda.nvtx.range_pop()
     peak, peak_kind = measured_peaks()
     achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
@@ -469,7 +486,7 @@ def main():
 
     batched = serving = None
     if rank == 0 and args.batch_sims > 0:
-        batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune)
+        batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 

@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--batch-sims", type=int, default=256, help="batched workload: 40^3 samples (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=150)
     ap.add_argument("--batch-only", action="store_true", help="run only the batched workload")
+    ap.add_argument("--layered-steps", type=int, default=10,
+                    help="200^3 layered cube: time steps of its FP32-refined and FP64 legs (0: skip)")
+    ap.add_argument("--layered-only", action="store_true", help="run only the 200^3 layered legs")
     ap.add_argument("--serve-requests", type=int, default=40, help="serving stream length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
@@ -320,6 +323,48 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tunin
             s.close()
 
 
+def run_layered(hg, torch, nsteps: int, stream, tune=True):
+    """The 200^3 layered cube (8,120,601 DOF, k 1:1000 layers and 0.01 pockets,
+    Dirichlet 1 on z=0, dt=5e-4, theta=0.5, rtol 1e-10): its first `nsteps`
+    steps in FP32-refined and in FP64, timed with CUDA events, plus the
+    dominant kernel of each timed alone after an L2 flush."""
+    import numpy as np
+    import workloads as W
+    p = W.layered_cube(nsteps=nsteps)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peak, _ = measured_peaks()
+    out = {"workload": f"layered_cube_200 (8,120,601 DOF), first {nsteps} of its 100 steps, dt=5e-4, theta=0.5, rtol 1e-10"}
+    fields = {}
+    for precision in ("fp32_refined", "fp64"):
+        tuning = autotune(hg, p, precision, stream) if tune else None
+        with hg.Simulation.from_problem(p, precision=precision, stream=stream.cuda_stream) as s:
+            s.step(1)  # warm-up (graph capture)
+            hg.heat_set_state(s.sim, p.u0, s.n_nodes)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = s.step(nsteps)
+            e.record(stream)
+            e.synchronize()
+            sec = a.elapsed_time(e) / 1e3
+            fields[precision] = s.state()
+            torch.cuda.nvtx.range_push(f"roofline_layered_{precision}")  # ncu captures filter on this range
+            prof = hg.heat_profile_iteration(s.sim, 20, flush)
+            torch.cuda.nvtx.range_pop()
+        achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
+        out[precision] = {"seconds": sec, "ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
+                          "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec, "kernel_tuning": tuning,
+                          "apply": {"ms_per_launch": prof["ms_apply"], "achieved_gbs": achieved, "peak_gbs": peak,
+                                    "frac": achieved / peak, "algorithmic_bytes_per_launch": prof["bytes_apply"]},
+                          "update": {"ms_per_launch": prof["ms_update"],
+                                     "achieved_gbs": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9
+                                     if prof["ms_update"] > 0 else None}}
+    u32, u64 = fields["fp32_refined"], fields["fp64"]
+    out["final_field_rel_err_fp32_refined_vs_fp64"] = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
+    return out
+
+
 def run_serving(hg, nreq: int, rate: float, budget_gb: float):
     """Poisson arrivals of serving_request(r) (edge U{20..120}, two-phase k,
     50..300 steps, rtol 1e-8, fp32_refined) at `rate` per second."""
@@ -384,6 +429,13 @@ def main():
     import workloads as W
 
     stream = torch.cuda.current_stream()
+    if args.layered_only:  # the 200^3 layered legs alone (used for profiling captures)
+        if args.tuning_json:
+            t = json.loads(args.tuning_json)
+            hg.heat_tuning_set(t["variant"], t["seg_nodes"])
+        print(json.dumps({"layered": run_layered(hg, torch, args.layered_steps, stream,
+                                                 not (args.no_autotune or args.tuning_json))}), flush=True)
+        return
     if args.batch_only:  # the batched workload alone (used for profiling captures)
         fixed = bool(args.tuning_json)
         if fixed:
@@ -484,9 +536,11 @@ def main():
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
     traffic = ncu_traffic(kernel_key)
 
-    batched = serving = None
+    batched = serving = layered = None
     if rank == 0 and args.batch_sims > 0:
         batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
+    if rank == 0 and args.layered_steps > 0:
+        layered = run_layered(hg, torch, args.layered_steps, stream, not (args.no_autotune or fixed))
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 
@@ -515,6 +569,7 @@ def main():
             "fp64_path": fp64,
             "final_field_rel_err_vs_fp64_path": final_err,
             "batched": batched,
+            "layered": layered,
             "serving": serving,
         }
         if cpu is not None:

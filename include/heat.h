@@ -77,6 +77,9 @@ typedef struct {
   double inner_rtol; /* FP32_REFINED: inner solve tolerance relative
                         to its own right-hand side                   [1e-4] */
   int max_outer;     /* FP32_REFINED: refinement sweeps per step     [40] */
+  int inner_max_iter; /* FP32_REFINED: CG iterations per inner solve;
+                         a restart loses the Krylov space, so stiff
+                         systems want long inner solves, >= 1        [2000] */
 } heat_params;
 
 /* Boundary conditions (§3.1 strong form: k dT/dn = f on the sides). */

@@ -41,7 +41,8 @@ class HeatError(RuntimeError):
 class heat_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("dt", C.c_double), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("resid_period", C.c_int), ("poll_period", C.c_int),
-                ("precision", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int)]
+                ("precision", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
+                ("inner_max_iter", C.c_int)]
 
 
 class heat_bc(C.Structure):

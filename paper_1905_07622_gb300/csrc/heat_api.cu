@@ -58,6 +58,7 @@ extern "C" void heat_params_default(heat_params* p) {
   p->precision = HEAT_FP64;
   p->inner_rtol = 1e-5;
   p->max_outer = 40;
+  p->inner_max_iter = 2000;
 }
 
 extern "C" heat_status heat_create_mesh(int nx, int ny, int nz, const double origin[3],
@@ -167,6 +168,7 @@ static heat_status check_params(const heat_params* p) {
   if (p->precision == HEAT_FP32_REFINED) {
     if (!(p->inner_rtol > 0.0 && p->inner_rtol < 1.0)) return set_error(HEAT_ERR_ARG, "inner_rtol must be in (0, 1)");
     if (p->max_outer < 1) return set_error(HEAT_ERR_ARG, "max_outer must be >= 1");
+    if (p->inner_max_iter < 1) return set_error(HEAT_ERR_ARG, "inner_max_iter must be >= 1");
   }
   return HEAT_OK;
 }
@@ -180,6 +182,7 @@ static void fill_params(heat_sim* s) {
   d.max_iter = s->prm.max_iter;
   d.resid_period = s->prm.resid_period;
   d.max_outer = s->prm.max_outer;
+  d.inner_max_iter = s->prm.inner_max_iter;
   d.prec = s->prm.precision;
 }
 

@@ -69,6 +69,7 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   uint32_t dir_faces;         // Dirichlet face bits
   int prec;                   // Prec
   int max_iter, resid_period, max_outer, flux_steps;
+  int inner_max_iter, pad_prm_;
   double g[6];                // Dirichlet values
   double inv_dt, theta, rtol, inner_rtol;
   double mhat[8], khat[8];    // element mass/stiffness entry by corner XOR pattern

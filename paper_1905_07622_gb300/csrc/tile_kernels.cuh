@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_cg_iter(const SimDev* __re
         sc->iter_step += 1;
         sc->cgs = nslot;
         sc->delta = gam;
-        const int cap = (s.prec == P_FP32_PLAIN) ? s.max_iter : s.resid_period;
+        const int cap = (s.prec == P_FP32_PLAIN) ? s.max_iter : s.inner_max_iter;
         if (sc->iter_step >= s.max_iter) {
           fail(sc, ST_NOT_CONVERGED);
         } else if (gam <= sc->thresh_in || sc->iter >= cap) {
@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict_
           if (dn <= sc->thresh) close_step(s, sc, dn);
           else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
         } else {
-          const int cap = (P == P_FP32_PLAIN) ? s.max_iter : s.resid_period;
+          const int cap = (P == P_FP32_PLAIN) ? s.max_iter : s.inner_max_iter;
           if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
           else if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
         }

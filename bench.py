@@ -432,7 +432,7 @@ def main():
     if args.layered_only:  # the 200^3 layered legs alone (used for profiling captures)
         if args.tuning_json:
             t = json.loads(args.tuning_json)
-            hg.heat_tuning_set(t["variant"], t["seg_nodes"])
+            hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
         print(json.dumps({"layered": run_layered(hg, torch, args.layered_steps, stream,
                                                  not (args.no_autotune or args.tuning_json))}), flush=True)
         return
@@ -440,7 +440,7 @@ def main():
         fixed = bool(args.tuning_json)
         if fixed:
             t = json.loads(args.tuning_json)
-            hg.heat_tuning_set(t["variant"], t["seg_nodes"])
+            hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
         print(json.dumps({"batched": run_batch(hg, torch, args.batch_sims, args.batch_steps, stream,
                                                not args.no_autotune, fixed)}), flush=True)
         return
@@ -449,7 +449,7 @@ def main():
     fixed = bool(args.tuning_json)
     if fixed:
         t = json.loads(args.tuning_json)
-        hg.heat_tuning_set(t["variant"], t["seg_nodes"])
+        hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
         tuning = {"table": hg.heat_tuning_get(), "set_by": "--tuning-json"}
     else:
         tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream)

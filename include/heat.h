@@ -310,10 +310,13 @@ heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flus
  *     (0 .. heat_tuning_num_variants()-1) or -1 for the block-tile apply.
  *     Default {-1, 0, 0}.
  *   seg_nodes[b]: output nodes per warp-segment tile for meshes of bucket b
- *     (N < 200000, N < 4000000, larger); 32 .. 2^20, default 512. */
+ *     (N < 200000, N < 4000000, larger); 32 .. 2^20, default 512.
+ *   pw_quads[p]: for heat_precision p, groups of 4 nodes each thread of the
+ *     pointwise update kernel handles (1, 2 or 4; default {2, 4, 4}). */
 typedef struct heat_tuning {
   int variant[3];
   int seg_nodes[3];
+  int pw_quads[3];
 } heat_tuning;
 int heat_tuning_num_variants(void);
 /* Shape of variant v: segment width in nodes along x (one lane per node),

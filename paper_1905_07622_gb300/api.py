@@ -67,10 +67,10 @@ class heat_request(C.Structure):
 
 
 class heat_tuning(C.Structure):
-    _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3)]
+    _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3), ("pw_quads", C.c_int * 3)]
 
     def as_dict(self):
-        return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes)}
+        return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes), "pw_quads": list(self.pw_quads)}
 
 
 class heat_server_stats(C.Structure):
@@ -478,9 +478,12 @@ def heat_tuning_get() -> dict:
     return t.as_dict()
 
 
-def heat_tuning_set(variant, seg_nodes):
+def heat_tuning_set(variant, seg_nodes, pw_quads=None):
+    """Set the table; pw_quads=None keeps the current pointwise item sizes."""
     load_library()
-    t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes))
+    if pw_quads is None:
+        pw_quads = heat_tuning_get()["pw_quads"]
+    t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes), (C.c_int * 3)(*pw_quads))
     _check(_lib.heat_tuning_set(C.byref(t)))
 
 

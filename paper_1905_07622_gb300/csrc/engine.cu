@@ -36,8 +36,8 @@ struct KernelSet {
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
-  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P>, SX, SY, SX * SY, SX * SY, nullptr, 0, 0, 0,
-          pw_chunk<T>(), {512, 512, 512}, 0, false};
+  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P, sizeof(T) == 4 ? 4 : 2>, SX, SY, SX * SY,
+          SX * SY, nullptr, 0, 0, 0, pw_chunk(sizeof(T) == 4 ? 4 : 2), {512, 512, 512}, 0, false};
 }
 
 // Warp-segment apply variants the tuner chooses from: segment width, rows per
@@ -78,7 +78,7 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // variant per precision (-1: the block-tile apply) and the segment tile size
 // per mesh-size bucket. Both are fixed per simulation size, so results stay
 // bitwise identical alone and in batches built under the same table.
-static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}};
+static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}};
 static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }
@@ -107,12 +107,27 @@ heat_status tuning_set(const Tuning& t) {
     if (v < -1 || v >= kNumVariants || (v >= 0 && p == P_FP64 && !kVariants[v].f64))
       return set_error(HEAT_ERR_ARG, "tuning: bad variant %d for precision %d", v, p);
   }
+  for (int p = 0; p < 3; ++p)
+    if (t.pw_quads[p] != 1 && t.pw_quads[p] != 2 && t.pw_quads[p] != 4)
+      return set_error(HEAT_ERR_ARG, "tuning: pointwise groups %d not 1, 2 or 4", t.pw_quads[p]);
   for (int b = 0; b < 3; ++b)
     if (t.seg_nodes[b] < 32 || t.seg_nodes[b] > (1 << 20))
       return set_error(HEAT_ERR_ARG, "tuning: segment size %d out of range", t.seg_nodes[b]);
   std::lock_guard<std::mutex> lock(g_tuning_mu);
   g_tuning = t;
   return HEAT_OK;
+}
+
+template <class T, int P>
+static TileFn update_for(int qpt) {
+  return qpt == 1 ? k_update<T, P, 1> : (qpt == 2 ? k_update<T, P, 2> : k_update<T, P, 4>);
+}
+static TileFn update_kernel(int prec, int qpt) {
+  switch (prec) {
+    case P_FP64: return update_for<double, P_FP64>(qpt);
+    case P_FP32_REFINED: return update_for<float, P_FP32_REFINED>(qpt);
+    default: return update_for<float, P_FP32_PLAIN>(qpt);
+  }
 }
 
 static KernelSet kernel_set(int prec, const Tuning& t) {
@@ -134,6 +149,9 @@ static KernelSet kernel_set(int prec, const Tuning& t) {
     }
   }
   for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
+  const int qpt = t.pw_quads[prec];
+  k.pw_chunk = pw_chunk(qpt);
+  k.update = update_kernel(prec, qpt);
   return k;
 }
 
@@ -776,6 +794,24 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
         best_t = ms;
         best = t;
       }
+    }
+  }
+  // then the pointwise kernel's item size with the chosen apply
+  const Tuning chosen = best;
+  for (int qpt : {1, 2, 4}) {
+    if (st != HEAT_OK || qpt == chosen.pw_quads[prec]) continue;
+    Tuning t = chosen;
+    t.pw_quads[prec] = qpt;
+    Engine* e = nullptr;
+    st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
+    if (st != HEAT_OK) break;
+    double ms = 0.0;
+    st = engine_time_iterations(e, 8, &ms);
+    if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
+    engine_destroy(e);
+    if (st == HEAT_OK && ms < best_t) {
+      best_t = ms;
+      best = t;
     }
   }
   if (st != HEAT_OK) return st;

@@ -57,6 +57,7 @@ void sim_stats(const heat_sim* s, heat_step_stats* o);
 struct Tuning {
   int variant[3];
   int seg_nodes[3];
+  int pw_quads[3];  // k_update: groups of 4 nodes per thread (1, 2 or 4), per precision
 };
 int size_bucket(long long nn);
 int num_variants();

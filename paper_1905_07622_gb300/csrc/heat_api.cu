@@ -708,6 +708,7 @@ extern "C" heat_status heat_tuning_get(heat_tuning* t) {
   for (int i = 0; i < 3; ++i) {
     t->variant[i] = x.variant[i];
     t->seg_nodes[i] = x.seg_nodes[i];
+    t->pw_quads[i] = x.pw_quads[i];
   }
   return HEAT_OK;
 }
@@ -718,6 +719,7 @@ extern "C" heat_status heat_tuning_set(const heat_tuning* t) {
   for (int i = 0; i < 3; ++i) {
     x.variant[i] = t->variant[i];
     x.seg_nodes[i] = t->seg_nodes[i];
+    x.pw_quads[i] = t->pw_quads[i];
   }
   return tuning_set(x);
 }

@@ -180,39 +180,4 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   }
 }
 
-// Publish this tile's partial sums and report whether the calling block
-// finished the simulation's last tile of this kernel. Only thread 0's return
-// value is meaningful; the caller broadcasts it. The last block then sums the
-// partials in tile order, so the result does not depend on which blocks ran
-// which tiles or on what else shares the launch.
-template <int NV>
-__device__ __forceinline__ bool publish_partials(const SimDev& s, int tile, const double (&v)[NV]) {
-  bool last = false;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s.partial[2 * tile + a] = v[a];
-    __threadfence();
-    unsigned int done = atomicAdd(&s.sc->count, 1u);
-    last = (done == (unsigned int)(s.ntiles - 1));
-    if (last) __threadfence();
-  }
-  return last;
-}
-
-// Ordered sum of the published partials (called by the last block).
-template <int NV>
-__device__ __forceinline__ void gather_partials(const SimDev& s, double (&out)[NV], double* red) {
-  double v[NV];
-#pragma unroll
-  for (int a = 0; a < NV; ++a) v[a] = 0.0;
-  // fixed assignment of tiles to threads and a fixed reduction tree
-  for (int t = threadIdx.x; t < s.ntiles; t += blockDim.x) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) v[a] += __ldcg(&s.partial[2 * t + a]);
-  }
-  block_sum<NV>(v, red);
-#pragma unroll
-  for (int a = 0; a < NV; ++a) out[a] = v[a];
-}
-
 }  // namespace heat

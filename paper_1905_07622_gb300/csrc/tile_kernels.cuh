@@ -26,10 +26,15 @@
 namespace heat {
 
 constexpr int kPwThreads = 256;
-// Nodes per pointwise work item: 16 per thread in FP32, 8 in FP64 (four
-// resp. two float4/double2 groups of 4 nodes, all loaded before any is used).
-template <class T> __host__ __device__ constexpr int pw_quads() { return sizeof(T) == 4 ? 4 : 2; }
-template <class T> __host__ __device__ constexpr int pw_chunk() { return kPwThreads * 4 * pw_quads<T>(); }
+// Nodes per pointwise work item: QPT groups of 4 nodes per thread (float4 /
+// two double2 each), all loaded before any is used. Fewer groups per thread
+// mean more, smaller items and more resident blocks (the tuning table picks
+// QPT per precision).
+__host__ __device__ constexpr int pw_chunk(int qpt) { return kPwThreads * 4 * qpt; }
+// Blocks per SM the register bound of k_update aims at, by QPT and value size.
+__host__ __device__ constexpr int pw_min_blocks(int qpt, int bytes) {
+  return bytes == 4 ? (qpt == 1 ? 4 : (qpt == 2 ? 3 : 2)) : (qpt == 1 ? 3 : (qpt == 2 ? 2 : 1));
+}
 
 // Control scalars of a simulation (written only by earlier kernels, or by
 // the last block after all of the simulation's items of this kernel).
@@ -148,9 +153,22 @@ __device__ __forceinline__ bool finish_item(const SimDev& s, int item, int nitem
   double t[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) t[a] = 0.0;
-  for (int u = threadIdx.x; u < nitems; u += 32) {
+  // Lane l adds items l, l+32, l+64, ... in that order; the loads of a batch
+  // of 8 are all issued before the first add, so the tail is a few L2 round
+  // trips instead of one per 32 items.
+  constexpr int B = 8;
+  for (int u0 = threadIdx.x; u0 < nitems; u0 += 32 * B) {
+    double v[B][NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) t[a] += __ldcg(&s.partial[4 * u + a]);
+    for (int k = 0; k < B; ++k) {
+      const int u = u0 + 32 * k;
+#pragma unroll
+      for (int a = 0; a < NV; ++a) v[k][a] = u < nitems ? __ldcg(&s.partial[4 * u + a]) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) t[a] += v[k][a];
   }
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
@@ -768,8 +786,8 @@ template <> struct Quad<double> {
   }
 };
 
-template <class T, int P>
-__global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict__ sims, const int2* __restrict__ work,
+template <class T, int P, int QPT>
+__global__ void __launch_bounds__(kPwThreads, pw_min_blocks(QPT, sizeof(T))) k_update(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                        const int* __restrict__ nwork_p) {
   __shared__ double red[32];
   __shared__ ItemCache cache;
@@ -784,10 +802,9 @@ __global__ void __launch_bounds__(kPwThreads) k_update(const SimDev* __restrict_
     const Ctl& c = cache.c;
     if (c.phase != PH_ITER) continue;
     const bool resid_it = (P == P_FP64) && s.resid_period > 0 && c.iter > 0 && (c.iter % s.resid_period) == 0;
-    constexpr int QPT = pw_quads<T>();
     const int nn = (int)s.nn;
-    const int base = wi.y * pw_chunk<T>();
-    const int end = min(base + pw_chunk<T>(), nn);
+    const int base = wi.y * pw_chunk(QPT);
+    const int end = min(base + pw_chunk(QPT), nn);
     T* __restrict__ x = (P == P_FP64) ? reinterpret_cast<T*>(s.vec64[c.ix]) : reinterpret_cast<T*>(s.e32);
     T* __restrict__ r = const_cast<T*>(IterVecs<T>::r(s));
     const T* __restrict__ pinv = IterVecs<T>::pinv(s);

@@ -82,10 +82,11 @@ def test_tuning_table_host_logic(lib):
     with pytest.raises(api.HeatError):
         api.heat_tuning_variant(n)
     old = api.heat_tuning_get()
-    assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512]}
+    assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512], "pw_quads": [2, 4, 4]}
     try:
-        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048])
-        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048]}
+        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4])
+        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
+                                         "pw_quads": [1, 2, 4]}
         no64 = [v for v in range(n) if not shapes[v]["has_fp64"]]
         bad = [([-1, n, 0], [512] * 3), ([-2, 0, 0], [512] * 3), ([-1, 0, 0], [16, 512, 512]),
                ([-1, 0, 0], [512, 512, (1 << 20) + 1])]
@@ -95,7 +96,11 @@ def test_tuning_table_host_logic(lib):
             with pytest.raises(api.HeatError) as e:
                 api.heat_tuning_set(variant, seg)
             assert e.value.status == api.HEAT_ERR_ARG
+        for quads in ([3, 4, 4], [2, 0, 4], [2, 4, 8]):
+            with pytest.raises(api.HeatError):
+                api.heat_tuning_set([-1, 0, 0], [512] * 3, quads)
         # a rejected table leaves the last good one in place
-        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048]}
+        assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
+                                         "pw_quads": [1, 2, 4]}
     finally:
-        api.heat_tuning_set(old["variant"], old["seg_nodes"])
+        api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])

@@ -61,7 +61,7 @@ def restore_table():
     import paper_1905_07622_gb300 as hg
     old = hg.heat_tuning_get()
     yield
-    hg.heat_tuning_set(old["variant"], old["seg_nodes"])
+    hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
 
 
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp64"])

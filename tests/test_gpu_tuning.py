@@ -21,7 +21,7 @@ def restore_table():
     import paper_1905_07622_gb300 as hg
     old = hg.heat_tuning_get()
     yield
-    hg.heat_tuning_set(old["variant"], old["seg_nodes"])
+    hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
 
 
 def _problem():
@@ -55,16 +55,19 @@ def test_every_variant_and_segment_size_matches_oracle(precision, tol):
     p = _problem()
     ref = pins.oracle_steps(p)
     pid = hg.PRECISIONS[precision]
-    for v in _variants(precision == "fp64"):
-        for seg in ([512] if v < 0 else [64, 256, 2048]):
-            table = hg.heat_tuning_get()
-            table["variant"][pid] = v
-            table["seg_nodes"][0] = seg
-            hg.heat_tuning_set(table["variant"], table["seg_nodes"])
-            us = _solve(p, precision)
-            for n in range(1, p.nsteps + 1):
-                err = np.linalg.norm(us[n - 1] - ref.u[n]) / np.linalg.norm(ref.u[n])
-                assert err <= tol, (v, seg, n, err)
+    cases = [(v, seg, None) for v in _variants(precision == "fp64") for seg in ([512] if v < 0 else [64, 256, 2048])]
+    cases += [(-1, 512, 1), (-1, 512, 2), (-1, 512, 4)]  # every pointwise item size
+    for v, seg, quads in cases:
+        table = hg.heat_tuning_get()
+        table["variant"][pid] = v
+        table["seg_nodes"][0] = seg
+        if quads:
+            table["pw_quads"][pid] = quads
+        hg.heat_tuning_set(table["variant"], table["seg_nodes"], table["pw_quads"])
+        us = _solve(p, precision)
+        for n in range(1, p.nsteps + 1):
+            err = np.linalg.norm(us[n - 1] - ref.u[n]) / np.linalg.norm(ref.u[n])
+            assert err <= tol, (v, seg, quads, n, err)
 
 
 def test_batch_bitwise_equal_to_alone_under_a_tuned_table():

@@ -725,6 +725,19 @@ heat_status engine_profile(Engine* e, int reps, void* flush, size_t flush_bytes,
   return HEAT_OK;
 }
 
+heat_status prime_products(heat_sim* s, int nslots) {
+  constexpr int SX = 16, SY = 16, TZ = 8;
+  const SimDev& d = s->dev;
+  const int ntx = (d.nx + 1 + SX - 2) / (SX - 1), nty = (d.ny + 1 + SY - 2) / (SY - 1);
+  const int ntz = (d.nz + 1 + TZ - 1) / TZ;
+  const long long grid = (long long)ntx * nty * ntz;
+  if (grid > (1LL << 31) - 1) return set_error(HEAT_ERR_ARG, "prime_products: mesh too large");
+  for (int v = 0; v < nslots; ++v)
+    k_product<SX, SY><<<(unsigned)grid, SX * SY, 0, s->stream>>>(s->d_dev, d.vec64[v], d.yv[v], ntx, nty, TZ);
+  CUDA_TRY(cudaGetLastError());
+  return HEAT_OK;
+}
+
 heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
   const int chunk_ticks = std::max(1, 40 / e->iters_per_tick);  // below the inner cap
   cudaEvent_t a, b;

@@ -72,6 +72,9 @@ heat_status tuning_set(const Tuning& t);
 // precision and of the first one's size bucket.
 heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* best_variant, int* best_seg,
                             double* best_ms);
+// yv[v] = A' vec64[v] for slots v < nslots on the sim's stream (the stored
+// products a resumed FP32-path simulation needs; see k_product).
+heat_status prime_products(heat_sim* s, int nslots);
 // Mean ms per CG iteration over about `reps` iterations run through the
 // engine's captured tick graph (as a solve runs them), every member kept
 // iterating; leaves the members' solver state undefined.

@@ -196,6 +196,8 @@ static heat_status sim_refresh(heat_sim* s) {
   heat_status st = sim_upload_desc(s);
   if (st != HEAT_OK) return st;
   const int g = grid_for(s->nn, 256);
+  // the operator changes: stored products A' u of past states no longer hold
+  CUDA_TRY(cudaMemsetAsync(&s->d_sc->y_valid, 0, sizeof(int), s->stream));
   CUDA_TRY(cudaMemsetAsync(s->d_bad, 0, sizeof(unsigned int), s->stream));
   k_setup_coef32<<<grid_for(s->ne, 256), 256, 0, s->stream>>>(s->d_dev, s->ne, s->d_bad);
   k_setup_diag<<<g, 256, 0, s->stream>>>(s->d_dev);
@@ -282,6 +284,7 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   ALLOC(d.coef, (size_t)s->ne * sizeof(double2), const double2*);
   ALLOC(d.coef32, (size_t)s->ne * sizeof(float2), const float2*);
   for (int v = 0; v < 4; ++v) { ALLOC(d.vec64[v], N8, double*); }
+  for (int v = 0; v < 4; ++v) { ALLOC(d.yv[v], N8, double*); }
   ALLOC(d.b, N8, double*);
   ALLOC(d.r, N8, double*);
   ALLOC(d.q, N8, double*);
@@ -481,6 +484,13 @@ extern "C" heat_status heat_set_history(heat_sim* s, const double* u_prev, const
   CUDA_TRY(cudaGetLastError());
   s->h_sc->have_prev = u_prev2 ? 1 : 0;
   s->h_sc->step = step;
+  if (s->prm.precision != HEAT_FP64) {
+    // the next step's x0 product comes from the stored A' U^{n-1}, A' U^{n-2},
+    // as in an uninterrupted run (bitwise the same values)
+    st = prime_products(s, u_prev2 ? 2 : 1);
+    if (st != HEAT_OK) return st;
+    s->h_sc->y_valid = u_prev2 ? 3 : 1;
+  }
   return sim_write_scalars(s);
 }
 
@@ -516,8 +526,8 @@ heat_status heat::sim_prepare_steps(heat_sim* s, int nsteps) {
 }
 
 size_t heat::sim_footprint(long long nn, long long ne) {
-  // 12 FP64 and 9 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
-  return (size_t)nn * (12 * 8 + 9 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
+  // 16 FP64 and 9 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
+  return (size_t)nn * (16 * 8 + 9 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
          4096 * sizeof(int) + 1024;
 }
 

@@ -43,6 +43,8 @@ struct SimScalars {
   int max_iters_step;
   unsigned int count;  // tiles finished in the running kernel
   int cgs;             // FP32 fused iteration: current slot of r, w, s (0/1)
+  int y_valid;         // bit v: yv[v] holds A' vec64[v] (FP32 paths, see k_open)
+  int pad2_;
   double delta;    // r^T P^-1 r of the current solve
   double delta_b;  // b^T P^-1 b of the step
   double thresh;   // rtol^2 * delta_b
@@ -83,6 +85,7 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   const double2* coef;        // (rho_c, k) per element
   const float2* coef32;
   double* vec64[4];           // U^{n-1}, U^{n-2}, x and spare (slots in SimScalars)
+  double* yv[4];              // A' vec64[v] where SimScalars.y_valid says so
   double* b;
   double* r;
   double* q;

@@ -39,7 +39,7 @@ __host__ __device__ constexpr int pw_min_blocks(int qpt, int bytes) {
 // Control scalars of a simulation (written only by earlier kernels, or by
 // the last block after all of the simulation's items of this kernel).
 struct Ctl {
-  int phase, iu1, iu2, ix, ixa, id, restart, have_prev, iter, step, cgs;
+  int phase, iu1, iu2, ix, ixa, id, restart, have_prev, iter, step, cgs, y_valid;
   double alpha, beta;
 };
 
@@ -56,6 +56,7 @@ __device__ __forceinline__ Ctl load_ctl(const SimScalars* sc) {
   c.iter = __ldcg(&sc->iter);
   c.step = __ldcg(&sc->step);
   c.cgs = __ldcg(&sc->cgs);
+  c.y_valid = __ldcg(&sc->y_valid);
   c.alpha = __ldcg(&sc->alpha);
   c.beta = __ldcg(&sc->beta);
   return c;
@@ -181,7 +182,11 @@ __device__ __forceinline__ bool finish_item(const SimDev& s, int item, int nitem
 
 // Step close, run by one thread: log, rotate the state ring
 // (U^{n-2} <- U^{n-1} <- x; the old U^{n-2} slot becomes the next x).
-__device__ __forceinline__ void close_step(const SimDev& s, SimScalars* sc, double delta_final) {
+// y_fresh: yv[ix] holds A' x (the closing FP64 residual pass computed it), so
+// the next step's x0 product needs no operator pass; the stored product of
+// U^{n-1} carries over to U^{n-2}.
+__device__ __forceinline__ void close_step(const SimDev& s, SimScalars* sc, double delta_final, bool y_fresh = false) {
+  sc->y_valid = (sc->y_valid & (1 << sc->iu1)) | (y_fresh ? (1 << sc->ix) : 0);
   const int st = sc->step;
   if (s.iters_log_len > 0) s.iters_log[st % s.iters_log_len] = sc->iter_step;
   sc->iters_total += sc->iter_step;
@@ -268,21 +273,40 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       const bool flux_on = s.flux_steps < 0 || c.step + 1 <= s.flux_steps;
       const double* __restrict__ F = s.F;
       const double* __restrict__ lift = s.zlift;
+      // On the FP32 paths the previous steps closed with an FP64 residual pass
+      // that also stored A' U^{n-1} (and A' U^{n-2}); then A' x0 = 2 A' U^{n-1}
+      // - A' U^{n-2} needs no operator pass and r is formed in pass 1.
+      const bool use_y =
+          P != P_FP64 && ((c.y_valid >> c.iu1) & 1) && (!hp || ((c.y_valid >> c.iu2) & 1));
+      const double* __restrict__ y1 = s.yv[c.iu1];
+      const double* __restrict__ y2 = s.yv[c.iu2];
       // pass 1: b = L u^{n-1} + F^n - A_{.D} g (free rows), g (Dirichlet rows)
       tile_op<double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta - 1.0, false, sh,
           [&](int m, bool live) -> double { return live ? u1[m] : 0.0; }, ident,
-          [&](int m, bool dir, double y, double) {
+          [&](int m, bool dir, double y, double v) {
             if (dir) {
               b[m] = dval(m);
+              if (use_y) {
+                x[m] = dval(m);
+                r32out[m] = 0.f;
+              }
             } else {
               const double bn = y + (flux_on ? F[m] : 0.0) - lift[m];
               b[m] = bn;
               part[1] += bn * bn * pinv[m];
+              if (use_y) {  // v = U^{n-1}_m
+                x[m] = hp ? 2.0 * v - u2[m] : v;
+                const double rn = bn - (hp ? 2.0 * y1[m] - y2[m] : y1[m]);
+                const float r32 = (float)rn;
+                r32out[m] = r32;
+                part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+                part[0] += rn * rn * pinv[m];
+              }
             }
           });
       // pass 2: x0 = 2u^{n-1} - u^{n-2} (u^{n-1} on the first step), r = b - A' x0
-      tile_op<double, SX, SY>(
+      if (!use_y) tile_op<double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> D2 {
             if (!live) return {0.0, 0.0};
@@ -310,6 +334,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       // x64 <- x64 + e32 (into the spare slot), r = b - A' x64 in FP64
       const double* __restrict__ x = s.vec64[c.ix];
       double* __restrict__ xa = s.vec64[c.ixa];
+      double* __restrict__ ya = s.yv[c.ixa];  // A' x64, used by the next step if this one closes
       const float* __restrict__ e32 = s.e32;
       tile_op<double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
@@ -324,6 +349,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
               xa[m] = dval(m);
             } else {
               xa[m] = v;
+              ya[m] = y;
               rn = b[m] - y;
             }
             const float r32 = (float)rn;
@@ -384,7 +410,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
           sc->delta = tot[2];
           const bool plain_done = (P == P_FP32_PLAIN && phase == PH_OUTER);
           if (tot[0] <= sc->thresh || plain_done || tot[2] <= 0.0) {
-            close_step(s, sc, tot[0]);
+            close_step(s, sc, tot[0], phase == PH_OUTER);
           } else if (sc->outer >= s.max_outer || sc->iter_step >= s.max_iter) {
             fail(sc, ST_NOT_CONVERGED);
           } else {
@@ -399,6 +425,32 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       }
     }
   }
+}
+
+// --------------------------------------------------------------- k_product
+
+// y = A' u on the free rows (Dirichlet rows and columns masked), with the
+// tile operator of k_open's residual passes, so the values are bitwise those
+// such a pass computes for the same u: a node's value does not depend on
+// where its tile starts. One block per tile of (SX-1) x (SY-1) node columns
+// and tz levels. Restores the stored products A' U^{n-1}, A' U^{n-2} of a
+// resumed simulation (see k_open, phase OPEN).
+template <int SX, int SY>
+__global__ void __launch_bounds__(SX* SY) k_product(const SimDev* __restrict__ sd, const double* __restrict__ u,
+                                                     double* __restrict__ y, int ntx, int nty, int tz) {
+  __shared__ TileSmem<double, SX, SY> sh;
+  const SimDev& s = *sd;
+  const Geo g(s);
+  const int t = blockIdx.x;
+  const int tx = t % ntx, rem = t / ntx, ty = rem % nty, tk = rem / nty;
+  const int k0 = tk * tz;
+  const int nzt = min(tz, s.nz + 1 - k0);
+  tile_op<double, SX, SY>(
+      g, s, s.coef, tx * (SX - 1), ty * (SY - 1), k0, nzt, s.inv_dt, s.theta, true, sh,
+      [&](int m, bool live) -> double { return live ? u[m] : 0.0; }, [](double v) { return v; },
+      [&](int m, bool dir, double yv, double) {
+        if (!dir) y[m] = yv;
+      });
 }
 
 // ------------------------------------------------------------- k_apply_dot

@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--layered-steps", type=int, default=10,
                     help="200^3 layered cube: time steps of its FP32-refined and FP64 legs (0: skip)")
     ap.add_argument("--layered-only", action="store_true", help="run only the 200^3 layered legs")
+    ap.add_argument("--mh-chains", type=int, default=32,
+                    help="corrosion inverse problem: Metropolis-Hastings chains solved as one batch (0: skip)")
+    ap.add_argument("--mh-iters", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=40, help="serving stream length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
@@ -365,6 +368,47 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True):
     return out
 
 
+def run_mh(hg, torch, nchains: int, niter: int, stream):
+    """The §5.3 inverse problem on a synthetic plate (corrosion_plate: 64 x 20 x 64
+    elements, 88,725 DOF, 100 steps of 0.1 s): camera data from the GPU forward
+    model at the true depth plus seeded noise, then nchains Metropolis-Hastings
+    chains whose proposals are solved as one batch per iteration (FP32-refined,
+    rtol 1e-10). Wall time of the chain steps (host accept/reject included)."""
+    import numpy as np
+    import workloads as W
+    pl = W.corrosion_plate()
+    geom = hg.make_corrosion(*(pl.geom[k] for k in ("z0", "half_width", "rho_c_sound", "k_sound", "rho_c_corr",
+                                                    "k_corr")))
+    p = pl.problem()
+    with hg.Simulation.from_problem(p, precision="fp64", stream=stream.cuda_stream) as s:
+        hg.heat_set_face_flux(s.sim, pl.flux_face, pl.flux_q)
+        hg.heat_set_coeffs_corrosion(s.sim, geom, pl.depth_true)
+        s.step(pl.nsteps)
+        u = s.state()
+    i = np.arange(pl.nx + 1)
+    k = np.arange(pl.nz + 1)
+    face = (i[None, :] + (pl.nx + 1) * (pl.ny + 1) * k[:, None]).ravel()  # y = 0, i fastest
+    data = pl.camera(u[face])
+    normals, uniforms = pl.draws(niter, nchains)
+    start = np.linspace(1.0, 11.0, nchains)
+    with hg.MHDriver(pl.nx, pl.ny, pl.nz, pl.extent, geom, data, pl.sigma, nchains, pl.nsteps, pl.depth_max,
+                     flux_face=pl.flux_face, flux_q=pl.flux_q, obs_face=pl.obs_face, u0=pl.u0, theta=pl.theta,
+                     dt=pl.dt, rtol=pl.rtol, precision="fp32_refined", stream=stream.cuda_stream) as mh:
+        ll0 = mh.loglik(start)  # also captures the batch's tick graph
+        solves0, iters0 = mh.stats()
+        t0 = time.perf_counter()
+        st, ll, dtr, ltr, acc = mh.run(niter, 0.5, normals, uniforms, start, ll0)
+        sec = time.perf_counter() - t0
+        solves, iters = mh.stats()
+    solves -= solves0
+    iters -= iters0
+    return {"workload": f"corrosion_plate 64x20x64 (88,725 DOF), {pl.nsteps} steps of {pl.dt} s, {nchains} chains x "
+                        f"{niter} Metropolis-Hastings steps, fp32_refined rtol {pl.rtol}, true depth {pl.depth_true} mm",
+            "seconds": sec, "mh_steps_per_s": niter * nchains / sec, "forward_solves_per_s": solves / sec,
+            "dof_cg_iters_per_s": p.n_nodes * iters / sec, "acceptance": float(acc.mean()),
+            "chain_mean_depth_last": float(st.mean())}
+
+
 def run_serving(hg, nreq: int, rate: float, budget_gb: float):
     """Poisson arrivals of serving_request(r) (edge U{20..120}, two-phase k,
     50..300 steps, rtol 1e-8, fp32_refined) at `rate` per second."""
@@ -536,11 +580,13 @@ def main():
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
     traffic = ncu_traffic(kernel_key)
 
-    batched = serving = layered = None
+    batched = serving = layered = mh = None
     if rank == 0 and args.batch_sims > 0:
         batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
     if rank == 0 and args.layered_steps > 0:
         layered = run_layered(hg, torch, args.layered_steps, stream, not (args.no_autotune or fixed))
+    if rank == 0 and args.mh_chains > 0:
+        mh = run_mh(hg, torch, args.mh_chains, args.mh_iters, stream)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 
@@ -570,6 +616,7 @@ def main():
             "final_field_rel_err_vs_fp64_path": final_err,
             "batched": batched,
             "layered": layered,
+            "inverse_problem": mh,
             "serving": serving,
         }
         if cpu is not None:

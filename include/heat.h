@@ -128,6 +128,10 @@ void heat_destroy_sim(heat_sim* sim);
 heat_status heat_set_coeffs(heat_sim* sim, const double* rho_c, const double* k,
                             int on_device);
 
+/* Copy the per-element coefficients out (Ne values each, element order;
+ * host or device buffers). Returns after the copy. */
+heat_status heat_get_coeffs(heat_sim* sim, double* rho_c, double* k, int on_device);
+
 /* Change dt / theta / tolerances / precision between steps. */
 heat_status heat_set_params(heat_sim* sim, const heat_params* params);
 
@@ -249,6 +253,96 @@ heat_status heat_diagonal(heat_sim* sim, double* p);
 heat_status heat_rhs(heat_sim* sim, int n, const double* u_prev, double* b);
 /* Face flux vector F (flux on), FP64, N values. */
 heat_status heat_flux_vector(heat_sim* sim, double* f);
+
+/* ---- the coefficient inverse problem (§5.3) -------------------------------
+ * §5.3 recovers a corrosion depth from surface temperatures: a heat source on
+ * the front face, the face's temperature after the heating time compared
+ * with noisy camera data, Metropolis-Hastings over the depth. These calls
+ * give the pieces on the device and a driver that runs many chains at once,
+ * every proposal's forward solve in one batch. */
+
+/* Non-uniform heat flux on one face: q holds one flux density per element
+ * face of `face` (0..5 = x=0, x=Lx, y=0, y=Ly, z=0, z=Lz), ordered with the
+ * lower tangential index fastest (face x: (j,k), face y: (i,k), face z:
+ * (i,j)). It replaces that face's uniform heat_bc flux; each node gets
+ * q*area/4 from each adjacent element face (the integral of the bilinear
+ * shape function, §3.1). The flux schedule (flux_steps) is unchanged.
+ * q = NULL restores the uniform value. Host or device input (copied). */
+heat_status heat_set_face_flux(heat_sim* sim, int face, const double* q, int on_device);
+
+/* A corrosion profile of depth `depth` (§5.3, the parabolic boundary of a
+ * gusset-plate crevice): seen from the rear face y = origin_y + Ly, the
+ * corrosion reaches depth(z) = depth * (1 - ((z - z0) / half_width)^2) for
+ * |z - z0| < half_width, and is the same along x. An element whose centroid
+ * (x_c, y_c, z_c) has (y_rear - y_c) < depth(z_c) takes the corroded
+ * material, every other element the sound one. Centroids and the test are
+ * evaluated in FP64 in exactly this operation order, without fused
+ * multiply-adds:
+ *   z_c = oz + (k + 0.5)*hz, t = (z_c - z0)/half_width, d = depth*(1 - t*t),
+ *   y_c = oy + (j + 0.5)*hy, corroded = |t| < 1 and (y_rear - y_c) < d. */
+typedef struct {
+  double z0, half_width;        /* apex height and half-width of the parabola */
+  double rho_c_sound, k_sound;  /* material outside the corrosion, > 0 */
+  double rho_c_corr, k_corr;    /* corroded material, > 0 */
+} heat_corrosion;
+/* Sets the coefficients from the profile on the device (no host round trip);
+ * otherwise as heat_set_coeffs. depth >= 0. */
+heat_status heat_set_coeffs_corrosion(heat_sim* sim, const heat_corrosion* geom, double depth);
+
+/* Log-likelihood of camera data on one face (§5.3: i.i.d. Gaussian pixel
+ * noise): *loglik = -1/2 sum_i ((U_i - data_i) / sigma)^2 over the face's
+ * nodes, U the current state. data: device, one value per face node with the
+ * lower tangential index fastest ((ny+1)*(nz+1) values for an x face, etc.).
+ * loglik: device, one double, written asynchronously on the sim's stream
+ * (a fixed-order sum: the same inputs give the same bits). */
+heat_status heat_face_loglik(heat_sim* sim, int face, const double* data, double sigma, double* loglik);
+
+/* Metropolis-Hastings over the corrosion depth with nchains chains that
+ * advance together; every chain's proposal is solved in one batch.
+ *   mesh: nx, ny, nz, origin, extent of the plate; bc: its boundary
+ *   conditions; params: the solver parameters; nsteps: time steps of the
+ *   heating period, starting from U = u0 (uniform). flux_face / flux_q: the
+ *   source as in heat_set_face_flux (host array). obs_face: the observed face;
+ *   data: host, one value per face node; sigma: noise std. depth_max: the
+ *   uniform prior's upper end (lower end 0). */
+typedef struct {
+  int nx, ny, nz;
+  double origin[3], extent[3];
+  heat_bc bc;
+  heat_params params;
+  int nsteps;
+  double u0;
+  int flux_face;
+  const double* flux_q;
+  heat_corrosion geom;
+  int obs_face;
+  const double* data;
+  double sigma;
+  double depth_max;
+  int nchains;
+} heat_mh_config;
+typedef struct heat_mh heat_mh;
+heat_status heat_mh_create(const heat_mh_config* cfg, void* cuda_stream, heat_mh** out);
+void heat_mh_destroy(heat_mh* mh);
+/* Log-likelihoods of nchains depths (one forward solve each, all in one
+ * batch). depths, loglik: host, nchains values. */
+heat_status heat_mh_loglik(heat_mh* mh, const double* depths, double* loglik);
+/* niter Metropolis-Hastings steps of every chain from `state` (host, nchains
+ * depths; updated in place) with log-likelihoods `state_ll` (host, nchains;
+ * NULL: computed first). Random draws are inputs: normals and uniforms hold
+ * niter*nchains values (iteration-major). Proposal depth' = depth +
+ * step * normal (rounded as a product, then a sum); a proposal outside
+ * [0, depth_max] is rejected (its chain's batch slot re-solves the current
+ * depth, whose result is discarded); otherwise it is accepted when
+ * log(uniform) < ll' - ll. Outputs per
+ * iteration and chain (iteration-major, host, may be NULL): the chain's depth
+ * and log-likelihood after the step and whether it accepted. */
+heat_status heat_mh_run(heat_mh* mh, int niter, double step, const double* normals, const double* uniforms,
+                        double* state, double* state_ll, double* depth_trace, double* ll_trace,
+                        int* accepted);
+/* Forward solves and CG iterations (all kinds, as heat_step_stats.iters) run
+ * by the driver so far (either pointer may be NULL). */
+heat_status heat_mh_stats(const heat_mh* mh, long long* solves, long long* cg_iters);
 
 /* ---- allocation-free operator call ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

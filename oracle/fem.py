@@ -131,6 +131,40 @@ def face_load(nx, ny, nz, extent, face: int, q: float) -> np.ndarray:
     return F
 
 
+def face_load_elements(nx, ny, nz, extent, face: int, q_elem) -> np.ndarray:
+    """F_i = int_face q phi_i ds for a flux density that is constant on each
+    element face of `face` (§3.1): q_elem[a + na*b] on the quad with lower
+    tangential index a and upper index b (na quads along the lower one).
+
+    The same 2x2 Gauss quadrature of the bilinear face functions as face_load.
+    """
+    n = (nx + 1) * (ny + 1) * (nz + 1)
+    F = np.zeros(n)
+    h = spacing(nx, ny, nz, extent)
+    axis = face // 2
+    dims = [d for d in range(3) if d != axis]
+    counts = (nx, ny, nz)
+    detJ = h[dims[0]] * h[dims[1]] / 4.0
+    corners = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    fixed = 0 if face % 2 == 0 else counts[axis]
+    na = counts[dims[0]]
+    q_elem = np.asarray(q_elem, dtype=np.float64)
+    for p in range(counts[dims[0]]):
+        for r in range(counts[dims[1]]):
+            q = q_elem[p + na * r]
+            for ca, cb in corners:
+                w = 0.0  # int of this corner's bilinear function times q over the quad
+                for a in _GP:
+                    for b in _GP:
+                        w += (1 + (2 * ca - 1) * a) * (1 + (2 * cb - 1) * b) / 4.0 * detJ
+                idx = [0, 0, 0]
+                idx[axis] = fixed
+                idx[dims[0]] = p + ca
+                idx[dims[1]] = r + cb
+                F[node_id(nx, ny, *idx)] += q * w
+    return F
+
+
 def flux_vector(p) -> np.ndarray:
     """Sum of the face loads of all Neumann flux faces of a Problem."""
     F = np.zeros(p.n_nodes)

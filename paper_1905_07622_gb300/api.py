@@ -66,6 +66,20 @@ class heat_request(C.Structure):
                 ("bc", heat_bc), ("params", heat_params), ("nsteps", C.c_int)]
 
 
+class heat_corrosion(C.Structure):
+    _fields_ = [("z0", C.c_double), ("half_width", C.c_double), ("rho_c_sound", C.c_double),
+                ("k_sound", C.c_double), ("rho_c_corr", C.c_double), ("k_corr", C.c_double)]
+
+
+class heat_mh_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("origin", C.c_double * 3), ("extent", C.c_double * 3),
+                ("bc", heat_bc), ("params", heat_params), ("nsteps", C.c_int), ("u0", C.c_double),
+                ("flux_face", C.c_int), ("flux_q", C.c_void_p), ("geom", heat_corrosion),
+                ("obs_face", C.c_int), ("data", C.c_void_p), ("sigma", C.c_double),
+                ("depth_max", C.c_double), ("nchains", C.c_int)]
+
+
 class heat_tuning(C.Structure):
     _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3), ("pw_quads", C.c_int * 3)]
 
@@ -130,6 +144,15 @@ _SIGS = [
     ("heat_tuning_set", C.c_int, [C.POINTER(heat_tuning)]),
     ("heat_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
     ("heat_batch_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
+    ("heat_get_coeffs", C.c_int, [_VP, _VP, _VP, C.c_int]),
+    ("heat_set_face_flux", C.c_int, [_VP, C.c_int, _VP, C.c_int]),
+    ("heat_set_coeffs_corrosion", C.c_int, [_VP, C.POINTER(heat_corrosion), C.c_double]),
+    ("heat_face_loglik", C.c_int, [_VP, C.c_int, _VP, C.c_double, _VP]),
+    ("heat_mh_create", C.c_int, [C.POINTER(heat_mh_config), _VP, C.POINTER(_VP)]),
+    ("heat_mh_destroy", None, [_VP]),
+    ("heat_mh_loglik", C.c_int, [_VP, _VP, _VP]),
+    ("heat_mh_run", C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("heat_mh_stats", C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     ("heat_last_error", C.c_char_p, []),
     ("heat_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -501,6 +524,111 @@ def heat_batch_autotune(batch, reps: int):
     ms = C.c_double()
     _check(_lib.heat_batch_autotune(batch, int(reps), C.byref(t), C.byref(ms)))
     return t.as_dict(), ms.value
+
+
+def make_corrosion(z0, half_width, rho_c_sound, k_sound, rho_c_corr, k_corr) -> heat_corrosion:
+    return heat_corrosion(float(z0), float(half_width), float(rho_c_sound), float(k_sound), float(rho_c_corr),
+                          float(k_corr))
+
+
+def heat_set_face_flux(sim, face: int, q, n_face_elems: int = 0):
+    """Per-element flux densities on one face (host array or CUDA tensor); q=None restores uniform."""
+    if q is None:
+        _check(_lib.heat_set_face_flux(sim, int(face), None, 0))
+        return
+    if hasattr(q, "data_ptr"):
+        _check(_lib.heat_set_face_flux(sim, int(face), C.c_void_p(_dev_ptr(q)), 1))
+    else:
+        a = np.ascontiguousarray(q, dtype=np.float64)
+        _check(_lib.heat_set_face_flux(sim, int(face), C.c_void_p(a.ctypes.data), 0))
+
+
+def heat_get_coeffs(sim, n_elems: int):
+    """(rho_c, k) per element as host arrays."""
+    rc = np.empty(n_elems)
+    kk = np.empty(n_elems)
+    _check(_lib.heat_get_coeffs(sim, C.c_void_p(rc.ctypes.data), C.c_void_p(kk.ctypes.data), 0))
+    return rc, kk
+
+
+def heat_set_coeffs_corrosion(sim, geom: heat_corrosion, depth: float):
+    _check(_lib.heat_set_coeffs_corrosion(sim, C.byref(geom), float(depth)))
+
+
+def heat_face_loglik(sim, face: int, data, sigma: float, out):
+    """-1/2 sum((U - data)/sigma)^2 over a face's nodes into out[0] (CUDA tensors)."""
+    _check(_lib.heat_face_loglik(sim, int(face), C.c_void_p(_dev_ptr(data)), float(sigma),
+                                 C.c_void_p(_dev_ptr(out))))
+
+
+class MHDriver:
+    """heat_mh_* (batched Metropolis-Hastings over the corrosion depth)."""
+
+    def __init__(self, nx, ny, nz, extent, geom, data, sigma, nchains, nsteps, depth_max, *, origin=(0, 0, 0),
+                 flux_face=-1, flux_q=None, obs_face=2, u0=0.0, dirichlet=None, flux=None, flux_steps=-1,
+                 stream=None, **params):
+        load_library()
+        cfg = heat_mh_config()
+        cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+        cfg.origin = (C.c_double * 3)(*origin)
+        cfg.extent = (C.c_double * 3)(*extent)
+        cfg.bc = make_bc(dirichlet or {}, flux or {}, flux_steps)
+        cfg.params = heat_params_default(**params)
+        cfg.nsteps = int(nsteps)
+        cfg.u0 = float(u0)
+        self._q = np.ascontiguousarray(flux_q, dtype=np.float64) if flux_q is not None else None
+        cfg.flux_face = int(flux_face) if self._q is not None else -1
+        cfg.flux_q = self._q.ctypes.data if self._q is not None else None
+        cfg.geom = geom
+        cfg.obs_face = int(obs_face)
+        self._data = np.ascontiguousarray(data, dtype=np.float64)
+        cfg.data = self._data.ctypes.data
+        cfg.sigma = float(sigma)
+        cfg.depth_max = float(depth_max)
+        cfg.nchains = int(nchains)
+        self.nchains = int(nchains)
+        self.h = C.c_void_p()
+        st = C.c_void_p(int(stream) if stream else 0)
+        _check(_lib.heat_mh_create(C.byref(cfg), st, C.byref(self.h)))
+
+    def loglik(self, depths):
+        d = np.ascontiguousarray(depths, dtype=np.float64)
+        out = np.empty(self.nchains)
+        _check(_lib.heat_mh_loglik(self.h, C.c_void_p(d.ctypes.data), C.c_void_p(out.ctypes.data)))
+        return out
+
+    def run(self, niter, step, normals, uniforms, state, state_ll=None):
+        """Returns (state, state_ll, depth_trace, ll_trace, accepted); traces are (niter, nchains)."""
+        n = self.nchains
+        nz = np.ascontiguousarray(normals, dtype=np.float64).reshape(niter * n)
+        un = np.ascontiguousarray(uniforms, dtype=np.float64).reshape(niter * n)
+        st = np.array(state, dtype=np.float64).copy()
+        ll = np.array(state_ll, dtype=np.float64).copy() if state_ll is not None else self.loglik(st)
+        dt = np.empty(niter * n)
+        lt = np.empty(niter * n)
+        acc = np.empty(niter * n, dtype=np.int32)
+        _check(_lib.heat_mh_run(self.h, int(niter), float(step), C.c_void_p(nz.ctypes.data),
+                                C.c_void_p(un.ctypes.data), C.c_void_p(st.ctypes.data),
+                                C.c_void_p(ll.ctypes.data), C.c_void_p(dt.ctypes.data),
+                                C.c_void_p(lt.ctypes.data), C.c_void_p(acc.ctypes.data)))
+        return st, ll, dt.reshape(niter, n), lt.reshape(niter, n), acc.reshape(niter, n).astype(bool)
+
+    def stats(self):
+        """(forward solves, CG iterations) so far."""
+        a, b = C.c_longlong(), C.c_longlong()
+        _check(_lib.heat_mh_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if self.h:
+            _lib.heat_mh_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def heat_last_error() -> str:

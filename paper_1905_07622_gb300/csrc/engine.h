@@ -29,6 +29,8 @@ struct heat_sim {
   heat::SimScalars* d_sc = nullptr;   // device scalars
   heat::SimScalars* h_sc = nullptr;   // pinned host mirror
   double* d_q6 = nullptr;
+  double* d_qface[6] = {};            // per-element face flux densities in use (NULL: uniform)
+  double* qface_buf[6] = {};          // their buffers (owned, in allocs)
   unsigned int* d_bad = nullptr;
   int iters_log_cap = 0;
   heat::Engine* eng = nullptr;        // single-simulation engine (lazy)
@@ -51,6 +53,13 @@ heat_status sim_prepare_steps(heat_sim* s, int nsteps);
 size_t sim_footprint(long long nn, long long ne);
 // Statistics from the host copy of the scalars (after sim_read_scalars).
 void sim_stats(const heat_sim* s, heat_step_stats* o);
+// Recompute the flux vector F from the uniform face values and the
+// per-element face arrays (asynchronous on the sim's stream).
+heat_status sim_setup_flux(heat_sim* s);
+// After the device coefficients changed: FP32 copy, Jacobi diagonal,
+// Dirichlet lift, stored products invalidated; no host round trip (the
+// caller guarantees valid coefficients).
+heat_status sim_derive_async(heat_sim* s);
 
 // Kernel tuning: warp-apply variant per precision (-1: block-tile apply) and
 // segment tile size (nodes) per mesh-size bucket (size_bucket).

@@ -192,6 +192,27 @@ heat_status heat::sim_upload_desc(heat_sim* s) {
 }
 
 // Recompute diag, lift and FP32 coefficients after coefficients/params change.
+heat_status heat::sim_setup_flux(heat_sim* s) {
+  const heat_mesh* m = s->mesh;
+  const double hx = m->extent[0] / m->nx, hy = m->extent[1] / m->ny, hz = m->extent[2] / m->nz;
+  FaceFlux ff;
+  for (int f = 0; f < 6; ++f) ff.q[f] = s->d_qface[f];
+  k_setup_flux<<<grid_for(s->nn, 256), 256, 0, s->stream>>>(s->d_dev, s->d_q6, ff, hx, hy, hz);
+  CUDA_TRY(cudaGetLastError());
+  return HEAT_OK;
+}
+
+heat_status heat::sim_derive_async(heat_sim* s) {
+  const int g = grid_for(s->nn, 256);
+  CUDA_TRY(cudaMemsetAsync(&s->d_sc->y_valid, 0, sizeof(int), s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->d_bad, 0, sizeof(unsigned int), s->stream));
+  k_setup_coef32<<<grid_for(s->ne, 256), 256, 0, s->stream>>>(s->d_dev, s->ne, s->d_bad);
+  k_setup_diag<<<g, 256, 0, s->stream>>>(s->d_dev);
+  k_setup_lift<<<g, 256, 0, s->stream>>>(s->d_dev);
+  CUDA_TRY(cudaGetLastError());
+  return HEAT_OK;
+}
+
 static heat_status sim_refresh(heat_sim* s) {
   heat_status st = sim_upload_desc(s);
   if (st != HEAT_OK) return st;
@@ -342,7 +363,8 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
     }
     st = sim_upload_desc(s);
     if (st != HEAT_OK) goto fail;
-    k_setup_flux<<<grid_for(s->nn, 256), 256, 0, s->stream>>>(s->d_dev, s->d_q6, hx, hy, hz);
+    st = sim_setup_flux(s);
+    if (st != HEAT_OK) goto fail;
     k_impose_dirichlet<<<grid_for(s->nn, 256), 256, 0, s->stream>>>(s->d_dev, d.vec64[0]);
     st = sim_refresh(s);
     if (st != HEAT_OK) goto fail;
@@ -401,6 +423,17 @@ extern "C" heat_status heat_set_coeffs(heat_sim* s, const double* rho_c, const d
   CUDA_TRY(cudaMemcpy2DAsync((char*)s->dev.coef + sizeof(double), sizeof(double2), s->dev.q, sizeof(double),
                              sizeof(double), (size_t)s->ne, cudaMemcpyDeviceToDevice, s->stream));
   return sim_refresh(s);
+}
+
+extern "C" heat_status heat_get_coeffs(heat_sim* s, double* rho_c, double* k, int on_device) {
+  if (!s || !rho_c || !k) return set_error(HEAT_ERR_ARG, "heat_get_coeffs: null argument");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpy2DAsync(rho_c, sizeof(double), s->dev.coef, sizeof(double2), sizeof(double), (size_t)s->ne,
+                             kind, s->stream));
+  CUDA_TRY(cudaMemcpy2DAsync(k, sizeof(double), (const char*)s->dev.coef + sizeof(double), sizeof(double2),
+                             sizeof(double), (size_t)s->ne, kind, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return HEAT_OK;
 }
 
 extern "C" heat_status heat_set_params(heat_sim* s, const heat_params* params) {

@@ -34,9 +34,28 @@ __global__ void k_setup_diag(const SimDev* __restrict__ sp) {
   }
 }
 
+// Per-element flux densities of the faces that have them (NULL: the face's
+// uniform value applies).
+struct FaceFlux {
+  const double* q[6];
+};
+
+// Sum of q over the 1, 2 or 4 element faces of a face grid (na x nb element
+// faces, index a + na*b) around node (a, b), in a fixed order.
+__device__ __forceinline__ double face_sum(const double* q, int na, int nb, int a, int b) {
+  double f = 0.0;
+  for (int db = -1; db <= 0; ++db)
+    for (int da = -1; da <= 0; ++da) {
+      const int ea = a + da, eb = b + db;
+      if (ea >= 0 && ea < na && eb >= 0 && eb < nb) f += q[ea + na * eb];
+    }
+  return f;
+}
+
 // Face flux vector F_i = int_face q phi_i ds: on a face of h_a*h_b quads each
-// node gets q*h_a*h_b/4 per adjacent quad (1, 2 or 4 of them).
-__global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __restrict__ q6,
+// node gets q*h_a*h_b/4 per adjacent quad (1, 2 or 4 of them), with q the
+// face's uniform value or the quad's own.
+__global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __restrict__ q6, FaceFlux ff,
                              double hx, double hy, double hz) {
   const SimDev& s = *sp;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
@@ -46,13 +65,14 @@ __global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __rest
     const int ni = (i > 0 && i < s.nx) ? 2 : 1;
     const int nj = (j > 0 && j < s.ny) ? 2 : 1;
     const int nk = (k > 0 && k < s.nz) ? 2 : 1;
+    const double ax = hy * hz * 0.25, ay = hx * hz * 0.25, az = hx * hy * 0.25;
     double f = 0.0;
-    if (i == 0) f += q6[0] * hy * hz * 0.25 * nj * nk;
-    if (i == s.nx) f += q6[1] * hy * hz * 0.25 * nj * nk;
-    if (j == 0) f += q6[2] * hx * hz * 0.25 * ni * nk;
-    if (j == s.ny) f += q6[3] * hx * hz * 0.25 * ni * nk;
-    if (k == 0) f += q6[4] * hx * hy * 0.25 * ni * nj;
-    if (k == s.nz) f += q6[5] * hx * hy * 0.25 * ni * nj;
+    if (i == 0) f += ff.q[0] ? face_sum(ff.q[0], s.ny, s.nz, j, k) * ax : q6[0] * ax * nj * nk;
+    if (i == s.nx) f += ff.q[1] ? face_sum(ff.q[1], s.ny, s.nz, j, k) * ax : q6[1] * ax * nj * nk;
+    if (j == 0) f += ff.q[2] ? face_sum(ff.q[2], s.nx, s.nz, i, k) * ay : q6[2] * ay * ni * nk;
+    if (j == s.ny) f += ff.q[3] ? face_sum(ff.q[3], s.nx, s.nz, i, k) * ay : q6[3] * ay * ni * nk;
+    if (k == 0) f += ff.q[4] ? face_sum(ff.q[4], s.nx, s.ny, i, j) * az : q6[4] * az * ni * nj;
+    if (k == s.nz) f += ff.q[5] ? face_sum(ff.q[5], s.nx, s.ny, i, j) * az : q6[5] * az * ni * nj;
     s.F[n] = is_dirichlet(s, i, j, k) ? 0.0 : f;
   }
 }

@@ -242,5 +242,81 @@ def random_box(nx: int, ny: int, nz: int, seed: int, extent=(1.0, 1.0, 1.0),
     return p
 
 
+@dataclass
+class CorrosionPlate:
+    """Synthetic stand-in for the corrosion-detection inverse problem of §5.3
+    (the paper's gusset-plate geometry and camera data are not available).
+
+    A steel plate of Lx x Ly x Lz mm (thickness Ly along y), front face y=0,
+    rear face y=Ly; corrosion (oxide) grows in from the rear face with a
+    parabolic profile in z of apex depth `depth`, constant along x. A Gaussian
+    laser spot of power `power` W and width `beam` mm heats the front face for
+    the whole period (nsteps of dt s, theta-scheme); the front face's
+    temperatures at the end are the observation. Units: mm, s, W, K; steel
+    k = 0.045 W/(mm K), rho*c = 3.6e-3 J/(mm^3 K); oxide k = 0.005,
+    rho*c = 3.5e-3 (textbook values, not the paper's garbled ones)."""
+
+    nx: int
+    ny: int
+    nz: int
+    extent: tuple
+    geom: dict
+    flux_face: int
+    flux_q: np.ndarray  # per element face of flux_face, lower tangential index fastest
+    nsteps: int
+    dt: float
+    theta: float
+    u0: float
+    obs_face: int
+    sigma: float
+    quantum: float
+    depth_true: float
+    depth_max: float
+    rtol: float
+    seed: int
+    origin: tuple = (0.0, 0.0, 0.0)
+
+    def problem(self) -> Problem:
+        """The forward problem with sound-steel coefficients (to be replaced)."""
+        ne = self.nx * self.ny * self.nz
+        nn = (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+        return Problem(f"corrosion_plate_{self.nx}x{self.ny}x{self.nz}", self.nx, self.ny, self.nz,
+                       origin=self.origin, extent=self.extent,
+                       rho_c=np.full(ne, self.geom["rho_c_sound"]), k=np.full(ne, self.geom["k_sound"]),
+                       u0=np.full(nn, self.u0), flux_steps=-1, theta=self.theta, dt=self.dt,
+                       nsteps=self.nsteps, rtol=self.rtol)
+
+    def camera(self, face_temps: np.ndarray) -> np.ndarray:
+        """Camera model of §5.3: i.i.d. N(0, sigma^2) noise (seeded), then
+        rounding to the camera's quantum."""
+        rng = np.random.default_rng(self.seed + 1)
+        noisy = np.asarray(face_temps) + rng.normal(0.0, self.sigma, len(face_temps))
+        return np.round(noisy / self.quantum) * self.quantum
+
+    def draws(self, niter: int, nchains: int, seed_offset: int = 0):
+        """Metropolis-Hastings draws: (normals, uniforms), each (niter, nchains)."""
+        rng = np.random.default_rng(self.seed + 2 + seed_offset)
+        return rng.standard_normal((niter, nchains)), rng.uniform(0.0, 1.0, (niter, nchains))
+
+
+def corrosion_plate(nx: int = 64, ny: int = 20, nz: int = 64, nsteps: int = 100, dt: float = 0.1,
+                    seed: int = 5001, power: float = 10.0, beam: float = 2.0, sigma: float = 0.1,
+                    quantum: float = 0.1, depth_true: float = 3.175, rtol: float = 1e-10) -> CorrosionPlate:
+    """40 x 12.7 x 40 mm plate, corrosion apex at z = 20 mm with half-width
+    15 mm, laser centred on the front face at (x, z) = (20, 20) mm; heating
+    for nsteps*dt s (10 s by default, as in §5.3) from 0 K above ambient."""
+    extent = (40.0, 12.7, 40.0)
+    hx, hz = extent[0] / nx, extent[2] / nz
+    xc = (np.arange(nx) + 0.5) * hx
+    zc = (np.arange(nz) + 0.5) * hz
+    X, Z = np.meshgrid(xc, zc)  # (nz, nx): x fastest, as the face's element order
+    r2 = (X - 20.0) ** 2 + (Z - 20.0) ** 2
+    q = power / (2.0 * np.pi * beam * beam) * np.exp(-r2 / (2.0 * beam * beam))
+    geom = {"z0": 20.0, "half_width": 15.0, "rho_c_sound": 3.6e-3, "k_sound": 0.045,
+            "rho_c_corr": 3.5e-3, "k_corr": 0.005}
+    return CorrosionPlate(nx, ny, nz, extent, geom, 2, q.ravel(), nsteps, dt, 0.5, 0.0, 2, sigma, quantum,
+                          depth_true, extent[1], rtol, seed)
+
+
 WORKLOADS: List[str] = ["two_phase_cube", "inclusions_cube", "lognormal_cube",
-                        "serving_request", "layered_cube"]
+                        "serving_request", "layered_cube", "corrosion_plate"]

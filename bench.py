@@ -316,7 +316,9 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tunin
                 "cg_iterations_per_sim_step": its / (nsims * nsteps),
                 "kernel_launches": stats[0]["kernel_launches"], "tuning": tuning,
                 "roofline": {"bound": "hbm", "kernel": "k_apply_dot<float>", "achieved": achieved, "peak": peak,
-                             "unit": "GB/s", "frac": achieved / peak, "ms_per_launch": prof["ms_apply"],
+                             "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": ncu_traffic("k_apply_dot<float>@lognormal_batch_256x40"),
+                             "ms_per_launch": prof["ms_apply"],
                              "algorithmic_bytes_per_launch": prof["bytes_apply"],
                              "update_kernel": {"ms_per_launch": prof["ms_update"],
                                                "achieved": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9}}}
@@ -359,7 +361,9 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True):
         out[precision] = {"seconds": sec, "ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
                           "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec, "kernel_tuning": tuning,
                           "apply": {"ms_per_launch": prof["ms_apply"], "achieved_gbs": achieved, "peak_gbs": peak,
-                                    "frac": achieved / peak, "algorithmic_bytes_per_launch": prof["bytes_apply"]},
+                                    "frac": achieved / peak, "algorithmic_bytes_per_launch": prof["bytes_apply"],
+                                    "traffic": ncu_traffic("k_apply_dot<float>@layered_cube_200")
+                                    if precision == "fp32_refined" else None},
                           "update": {"ms_per_launch": prof["ms_update"],
                                      "achieved_gbs": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9
                                      if prof["ms_update"] > 0 else None}}

@@ -67,7 +67,7 @@ extern "C" heat_status heat_create_mesh(int nx, int ny, int nz, const double ori
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1)
     return set_error(HEAT_ERR_ARG, "heat_create_mesh: nx, ny, nz must be >= 1 (got %d %d %d)", nx, ny, nz);
-  const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  const long long nn = ((long long)nx + 1) * ((long long)ny + 1) * ((long long)nz + 1);
   // node and element indices are 32-bit in the kernels
   if (nn >= (1LL << 31) - 1)
     return set_error(HEAT_ERR_ARG, "heat_create_mesh: %lld nodes; at most 2^31 - 2 per mesh", nn);

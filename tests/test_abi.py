@@ -54,6 +54,10 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert e.value.status == api.HEAT_ERR_ARG
     with pytest.raises(api.HeatError):
         api.heat_create_mesh(2, 2, 2, extent=(1.0, -1.0, 1.0))
+    for dims in [(2000, 2000, 2000), (2**31 - 1, 1, 1), (1290, 1290, 1290)]:  # >= 2^31 - 1 nodes
+        with pytest.raises(api.HeatError) as e:
+            api.heat_create_mesh(*dims)
+        assert e.value.status == api.HEAT_ERR_ARG
     m = api.heat_create_mesh(3, 4, 5)
     assert api.heat_mesh_sizes(m) == (4 * 5 * 6, 60)
     api.heat_destroy_mesh(m)

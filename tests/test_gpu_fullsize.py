@@ -64,6 +64,23 @@ def restore_table():
     hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
 
 
+def test_inclusions_100_tuned_steps_satisfy_step_equation(restore_table):
+    import paper_1905_07622_gb300 as hg
+    p = W.inclusions_cube(nsteps=3)
+    _tune(hg, p, "fp32_refined")  # the headline configuration, tuned as bench.py does
+    with hg.Simulation.from_problem(p, precision="fp32_refined") as s:
+        us = [s.state()]
+        for _ in range(3):
+            assert s.step(1)["status"] == 0
+            us.append(s.state())
+    rng = np.random.default_rng(4)
+    rows = _sample_rows(p, rng, 800)
+    for n in (1, 2, 3):
+        res, rhs = _step_residual(p, us[n - 1], us[n], n, rows)
+        rel = np.linalg.norm(res) / np.linalg.norm(rhs)
+        assert rel <= SAMPLED_BOUND, (n, rel)
+
+
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp64"])
 def test_layered_200_steps_satisfy_step_equation(precision, restore_table):
     import paper_1905_07622_gb300 as hg

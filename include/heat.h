@@ -446,6 +446,17 @@ heat_status heat_autotune(heat_sim* sim, int reps, heat_tuning* best, double* be
  * to rebuild leaves the batch unusable (destroy it). */
 heat_status heat_batch_autotune(heat_batch* batch, int reps, heat_tuning* best, double* best_ms);
 
+/* ---- compiled-in index checks (the library built with HEAT_CHECK) -------
+ * No GPU sanitizer runs on the target machines, so the library can be built
+ * a second time with HEAT_CHECK defined (build.py, checked=True, giving
+ * lib/libheatgb_check.so): its operator kernels test every node and element
+ * index they form against the simulation's bounds, skip an access that
+ * would fall outside and count it. heat_checks_compiled() says which build
+ * is loaded (1: checked); heat_check_violations gives a simulation's count
+ * since it was created (always 0 in the normal build). */
+int heat_checks_compiled(void);
+heat_status heat_check_violations(heat_sim* sim, unsigned int* count);
+
 const char* heat_last_error(void);
 const char* heat_status_string(heat_status s);
 

@@ -153,6 +153,8 @@ _SIGS = [
     ("heat_mh_loglik", C.c_int, [_VP, _VP, _VP]),
     ("heat_mh_run", C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("heat_mh_stats", C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    ("heat_checks_compiled", C.c_int, []),
+    ("heat_check_violations", C.c_int, [_VP, C.POINTER(C.c_uint)]),
     ("heat_last_error", C.c_char_p, []),
     ("heat_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -160,11 +162,14 @@ _SIGS = [
 EXPORTED = [name for name, _, _ in _SIGS]
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libheatgb.so (raises if it has not been built: no fallback)."""
+def load_library(path: str = None):
+    """Load libheatgb.so, or the library HEATGB_LIBRARY names (for example
+    the index-checked build lib/libheatgb_check.so); raises if it has not
+    been built: there is no fallback."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("HEATGB_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_1905_07622_gb300.build.build() "
                           "(the solver has no CPU fallback)")
@@ -629,6 +634,17 @@ class MHDriver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def heat_checks_compiled() -> bool:
+    load_library()
+    return bool(_lib.heat_checks_compiled())
+
+
+def heat_check_violations(sim) -> int:
+    n = C.c_uint()
+    _check(_lib.heat_check_violations(sim, C.byref(n)))
+    return n.value
 
 
 def heat_last_error() -> str:

@@ -244,7 +244,9 @@ heat_status heat::sim_write_scalars(heat_sim* s) {
 }
 
 static void reset_scalars(SimScalars* sc) {
+  const unsigned int checks = sc->check_violations;  // counted over the sim's life
   std::memset(sc, 0, sizeof(SimScalars));
+  sc->check_violations = checks;
   sc->phase = PH_IDLE;
   sc->iu1 = 0;
   sc->iu2 = 1;
@@ -341,6 +343,7 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
     st = set_error(HEAT_ERR_NOMEM, "cudaMallocHost failed");
     goto fail;
   }
+  s->h_sc->check_violations = 0;
   reset_scalars(s->h_sc);
   {
     // default state: rho_c = k = 1, U^0 = 0 (Dirichlet nodes at their values)
@@ -795,4 +798,22 @@ extern "C" heat_status heat_batch_autotune(heat_batch* b, int reps, heat_tuning*
   if (best) st = heat_tuning_get(best);
   if (best_ms) *best_ms = ms;
   return st;
+}
+
+// ------------------------------------------------------------ index checks
+
+extern "C" int heat_checks_compiled(void) {
+#ifdef HEAT_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" heat_status heat_check_violations(heat_sim* s, unsigned int* count) {
+  if (!s || !count) return set_error(HEAT_ERR_ARG, "heat_check_violations: null argument");
+  heat_status st = sim_read_scalars(s);
+  if (st != HEAT_OK) return st;
+  *count = s->h_sc->check_violations;
+  return HEAT_OK;
 }

@@ -44,7 +44,7 @@ struct SimScalars {
   unsigned int count;  // tiles finished in the running kernel
   int cgs;             // FP32 fused iteration: current slot of r, w, s (0/1)
   int y_valid;         // bit v: yv[v] holds A' vec64[v] (FP32 paths, see k_open)
-  int pad2_;
+  unsigned int check_violations;  // out-of-range indices met (HEAT_CHECK builds)
   double delta;    // r^T P^-1 r of the current solve
   double delta_b;  // b^T P^-1 b of the step
   double thresh;   // rtol^2 * delta_b
@@ -110,6 +110,21 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   int iters_log_len;
   SimScalars* sc;
 };
+
+// Compiled-in index checks (the library built with -DHEAT_CHECK): a node or
+// element index outside [0, n) is counted in SimScalars.check_violations and
+// the access it guards is skipped. In normal builds the test is the constant
+// true and costs nothing.
+#ifdef HEAT_CHECK
+__device__ __forceinline__ bool heat_index_ok(SimScalars* sc, long long idx, long long n) {
+  if (idx >= 0 && idx < n) return true;
+  atomicAdd(&sc->check_violations, 1u);
+  return false;
+}
+#define HEAT_INDEX_OK(sc, idx, n) ::heat::heat_index_ok((sc), (long long)(idx), (long long)(n))
+#else
+#define HEAT_INDEX_OK(sc, idx, n) true
+#endif
 
 // ---------------------------------------------------------------- helpers
 

@@ -149,6 +149,9 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
   }
   const int estride = g.nx * g.ny;
   const int ebase = elem_col ? i + g.nx * j : 0;
+  const long long nn_all = (long long)g.pxy * (g.nz + 1), ne_all = (long long)estride * g.nz;
+  (void)nn_all;
+  (void)ne_all;
   const int gnz = g.nz, pxy = g.pxy;
   const bool dz0 = (g.dir & 16u) != 0, dz1 = (g.dir & 32u) != 0;
   using Raw = decltype(fetch(0, false));
@@ -156,7 +159,9 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
     const bool kin = L >= 0 && L <= gnz;
     const bool dk = mask && ((dz0 && L == 0) || (dz1 && L == gnz));
     const int off = L * pxy;
-    auto live = [&](const Col& c) { return c.in && kin && !dk && !(mask && c.dxy); };
+    auto live = [&](const Col& c) {
+      return c.in && kin && !dk && !(mask && c.dxy) && HEAT_INDEX_OK(s.sc, c.base + off, nn_all);
+    };
     r00 = fetch(c00.base + off, live(c00));
     if (lastx) r10 = fetch(c10.base + off, live(c10));
     if (lasty) r01 = fetch(c01.base + off, live(c01));
@@ -167,7 +172,8 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
     CoefT c;
     c.x = T(0);
     c.y = T(0);
-    if (elem_col && E >= 0 && E < gnz) c = coef[ebase + estride * E];  // int: N < 2^31 per simulation
+    if (elem_col && E >= 0 && E < gnz && HEAT_INDEX_OK(s.sc, ebase + estride * E, ne_all))
+      c = coef[ebase + estride * E];  // int: N < 2^31 per simulation
     return c;
   };
   Raw r00 = fetch(0, false), r10 = r00, r01 = r00, r11 = r00;
@@ -216,7 +222,7 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
       const T nl = g0 + g1, nr = g0 - g1;
       const T from_left = __shfl_up_sync(FULL, nr, 1, SX);
       const int lv = L - 2;
-      if (outcol && lv <= gnz) {
+      if (outcol && lv <= gnz && HEAT_INDEX_OK(s.sc, c00.base + lv * pxy, nn_all)) {
         const bool dir = c00.dxy || (dz0 && lv == 0) || (dz1 && lv == gnz);
         out(c00.base + lv * pxy, dir, nl + from_left, vh2);
       }

@@ -55,8 +55,14 @@ struct LaneGeo {
   unsigned rin, rdxy, ein, rstat;  // bit r: row inside / x-y Dirichlet / element row valid / loadable
   int nbase, ebase, estride, pxy, gnz, px, enx;
   bool dz0, dz1, mask;
+  SimScalars* sc;      // where HEAT_CHECK builds count out-of-range indices
+  long long nn, ne;    // node and element counts (the index bounds)
 
-  __device__ __forceinline__ LaneGeo(const Geo& g, bool active, int lx, int SX, int i0, int j0, bool mask_) {
+  __device__ __forceinline__ LaneGeo(const Geo& g, bool active, int lx, int SX, int i0, int j0, bool mask_,
+                                     SimScalars* sc_ = nullptr) {
+    sc = sc_;
+    nn = (long long)g.px * (g.ny + 1) * (g.nz + 1);
+    ne = (long long)g.nx * g.ny * g.nz;
     const int c = i0 - 1 + lx;
     const bool col_in = active && c >= 0 && c <= g.nx;
     out_lane = active && lx >= 1 && lx <= SX - 2 && c <= g.nx;
@@ -110,7 +116,10 @@ struct RegSrc {
     const unsigned lv = lg.live_rows(L);
     const int off = lg.nbase + L * lg.pxy;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) raw[r] = fetch(off + r * lg.px, (lv >> r) & 1u);
+    for (int r = 0; r < NR; ++r) {
+      const int m = off + r * lg.px;
+      raw[r] = fetch(m, ((lv >> r) & 1u) && HEAT_INDEX_OK(lg.sc, m, lg.nn));
+    }
   }
   __device__ __forceinline__ void load_coef(const LaneGeo<NY>& lg, int E) {
     const unsigned le = lg.live_elems(E);
@@ -119,7 +128,8 @@ struct RegSrc {
       Coef z;
       z.x = T(0);
       z.y = T(0);
-      cf[r] = ((le >> r) & 1u) ? coef[lg.ebase + r * lg.enx + E * lg.estride] : z;
+      const int e = lg.ebase + r * lg.enx + E * lg.estride;
+      cf[r] = (((le >> r) & 1u) && HEAT_INDEX_OK(lg.sc, e, lg.ne)) ? coef[e] : z;
     }
   }
   // before the loop: node level k0-1, element layer k0-1 (used at t = 1)
@@ -199,7 +209,7 @@ struct AsyncSrc {
     const int off = lg.nbase + L * lg.pxy;
 #pragma unroll
     for (int row = 0; row < NR; ++row) {
-      const bool live = (lv >> row) & 1u;
+      const bool live = ((lv >> row) & 1u) && HEAT_INDEX_OK(lg.sc, off + row * lg.px, lg.nn);
       const int m = live ? off + row * lg.px : 0;
       cp_async<sizeof(T)>(node_slot(st, row, 0), pinv + m, live);
       cp_async<sizeof(T)>(node_slot(st, row, 1), r + m, live);
@@ -208,7 +218,8 @@ struct AsyncSrc {
     const unsigned le = lg.live_elems(E);
 #pragma unroll
     for (int row = 0; row < NF; ++row) {
-      const bool live = (le >> row) & 1u;
+      const bool live =
+          ((le >> row) & 1u) && HEAT_INDEX_OK(lg.sc, lg.ebase + row * lg.enx + E * lg.estride, lg.ne);
       const int e = live ? lg.ebase + row * lg.enx + E * lg.estride : 0;
       cp_async<sizeof(Coef)>(elem_slot(st, row), coef + e, live);
     }
@@ -326,9 +337,10 @@ __device__ __forceinline__ void warp_tile_march(const LaneGeo<NY>& lg, const Sim
           const T2 g = V::add(V::add(G[r][0], G[r][1]), V::fma(G[r - 1][1], M1, G[r - 1][0]));
           const T nl = g.x + g.y, nr = g.x - g.y;
           const T from_left = __shfl_up_sync(FULL, nr, 1, SX);
-          if (lg.out_lane && lvin && ((lg.rin >> r) & 1u)) {
+          const int m = lg.nbase + r * lg.px + lv * lg.pxy;
+          if (lg.out_lane && lvin && ((lg.rin >> r) & 1u) && HEAT_INDEX_OK(lg.sc, m, lg.nn)) {
             const bool dir = ((lg.rdxy >> r) & 1u) || dzl;
-            out(lg.nbase + r * lg.px + lv * lg.pxy, dir, nl + from_left, vprev[r - 1]);
+            out(m, dir, nl + from_left, vprev[r - 1]);
           }
         }
       }
@@ -347,7 +359,7 @@ template <class T, int SX, int NY, class Coef, class Fetch, class Value, class O
 __device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, const Coef* __restrict__ coef, bool active,
                                              int i0, int j0, int k0, int tzl, T sa, T sb, bool mask, Fetch&& fetch,
                                              Value&& value, Out&& out) {
-  const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, i0, j0, mask);
+  const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, i0, j0, mask, s.sc);
   using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
   RegSrc<T, NY, CoefT, typename std::remove_reference<Fetch>::type, typename std::remove_reference<Value>::type> src(
       coef, fetch, value, k0);

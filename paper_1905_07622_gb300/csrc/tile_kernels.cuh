@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
           [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
     } else {
       using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(IterVecs<T>::coef(s)[0])>::type>::type;
-      const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true);
+      const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
       AsyncSrc<T, NY, STAGES, CoefT> src(pinv, r, rs ? nullptr : dold, IterVecs<T>::coef(s), beta, stage_smem,
                                          (int)blockDim.x, (int)threadIdx.x, tz * s.w_tz);
       warp_tile_march<T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
@@ -651,8 +651,8 @@ struct CgSrc {
     const bool own = owned_level(lg, L);
 #pragma unroll
     for (int row = 0; row < NR; ++row) {
-      const bool live = (lv >> row) & 1u;
       const int m = off + row * lg.px;
+      const bool live = ((lv >> row) & 1u) && HEAT_INDEX_OK(lg.sc, m, lg.nn);
       Raw z = {0.f, 0.f, 0.f, 0.f};
       if (live) {
         z.r = r[m];
@@ -671,8 +671,10 @@ struct CgSrc {
   __device__ __forceinline__ void load_coef(const LaneGeo<NY>& lg, int E) {
     const unsigned le = lg.live_elems(E);
 #pragma unroll
-    for (int row = 0; row < NF; ++row)
-      cf[row] = ((le >> row) & 1u) ? coef[lg.ebase + row * lg.enx + E * lg.estride] : make_float2(0.f, 0.f);
+    for (int row = 0; row < NF; ++row) {
+      const int e = lg.ebase + row * lg.enx + E * lg.estride;
+      cf[row] = (((le >> row) & 1u) && HEAT_INDEX_OK(lg.sc, e, lg.ne)) ? coef[e] : make_float2(0.f, 0.f);
+    }
   }
   __device__ __forceinline__ void prologue(const LaneGeo<NY>& lg, int) {
     load_nodes(lg, k0 - 1);
@@ -693,7 +695,7 @@ struct CgSrc {
         const float sv = a.w + beta * a.so;  // so = 0 in mode 1
         const float rn = a.r - alpha * sv;
         v[row] = a.p * rn;
-        if (row >= 1 && row <= NY && own && ((lv >> row) & 1u)) {
+        if (row >= 1 && row <= NY && own && ((lv >> row) & 1u) && HEAT_INDEX_OK(lg.sc, off + row * lg.px, lg.nn)) {
           const int m = off + row * lg.px;
           const float pn = a.p * a.r + beta * pp[row - 1];
           rnew[m] = rn;
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_cg_iter(const SimDev* __re
     src.tzl = s.w_tz;
     float* __restrict__ wout = mode == 0 ? s.wc32[slot] : s.wc32[nslot];
     float del = 0.f;
-    const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true);
+    const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
     warp_tile_march<float, SX, NY>(lg, s, src, s.w_tz, (float)s.inv_dt, (float)s.theta,
                                    [&](int m, bool dir, float y, float v) {
                                      const float wv = dir ? 0.f : y;

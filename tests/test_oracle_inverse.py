@@ -122,3 +122,20 @@ def test_forward_independent_of_depth_for_one_material():
     pl = _tiny_plate()
     pl.geom = dict(pl.geom, rho_c_corr=pl.geom["rho_c_sound"], k_corr=pl.geom["k_sound"])
     assert np.array_equal(inverse.forward(pl, 0.0), inverse.forward(pl, 6.0))
+
+
+def test_forward_uses_the_corrosion_coefficients():
+    # all-covering corrosion must equal a plate built with the corroded
+    # material everywhere (coefficients set directly, not by the profile test)
+    pl = _tiny_plate()
+    pl.geom = dict(pl.geom, half_width=1e9)
+    u = inverse.forward(pl, 2.0 * pl.extent[1])
+    p = pl.problem()
+    p.rho_c[:] = pl.geom["rho_c_corr"]
+    p.k[:] = pl.geom["k_corr"]
+    from oracle import transient
+    S = transient.build_system(p)
+    S.F = fem.face_load_elements(p.nx, p.ny, p.nz, p.extent, pl.flux_face, pl.flux_q)
+    ref = transient.run(p, solver="direct", system=S).u[-1]
+    assert np.allclose(u, ref, rtol=1e-12, atol=0.0)
+    assert not np.array_equal(inverse.forward(_tiny_plate(), 0.0), u)

@@ -86,3 +86,46 @@ def test_preconditioned_cg_reaches_dense_solution_and_degree_cuts_iterations():
         assert np.linalg.norm(x - exact) <= 1e-9 * np.linalg.norm(exact)
     x, it = precond.pcg_precond(A, b, np.zeros_like(b), precond.ilu_preconditioner(A), 1e-12)
     assert np.linalg.norm(x - exact) <= 1e-9 * np.linalg.norm(exact) and it < its[0]
+
+
+@pytest.mark.parametrize("seed,extent,dirichlet", [(0, (1.0, 1.0, 1.0), {0: 0.0}), (1, (2.0, 0.5, 1.0), {}),
+                                                   (2, (1.0, 1.0, 3.0), {4: 1.0, 1: 0.0})])
+def test_element_bound_lies_above_assembled_gershgorin_and_spectrum(seed, extent, dirichlet):
+    p = W.random_box(4, 5, 3, seed=seed, extent=extent, dirichlet=dirichlet, contrast=(0.01, 100.0), dt=0.3)
+    S = transient.build_system(p)
+    lam, _, _ = _spectrum(S.A_ff, S.pinv_f)
+    g = precond.gershgorin_lam_max(S.A_ff, S.pinv_f)
+    e = precond.element_lam_max(p)
+    assert lam[-1] <= g * (1 + 1e-12) and g <= e * (1 + 1e-12)
+
+
+def test_element_bound_closed_forms():
+    # Q1 mass rows on a box sum to h^3/8 against a diagonal of h^3/27: 27/8;
+    # Q1 stiffness rows on a cube: diagonal h/3, absolute off-diagonal sum h/3: 2
+    p = W.random_box(3, 3, 3, seed=0, extent=(0.6, 0.9, 1.2), dt=1.0, contrast=(1.0, 1.0))
+    p.k[:] = 1e-300
+    assert abs(precond.element_lam_max(p) - 27.0 / 8.0) < 1e-13
+    p = W.random_box(3, 3, 3, seed=0, dt=1.0, contrast=(1.0, 1.0))
+    p.rho_c[:] = 1e-300
+    assert abs(precond.element_lam_max(p) - 2.0) < 1e-13
+
+
+def test_chebyshev_pcg_degree_one_is_algorithm_one_and_degree_cuts_iterations():
+    p = W.random_box(6, 5, 7, seed=4, dt=10.0, contrast=(0.01, 100.0), dirichlet={4: 1.0})
+    S = transient.build_system(p)
+    b = transient.step_rhs(p, S, p.u0, 1)
+    x0 = p.u0[S.free]
+    exact = pcg.solve_dense(S.A_ff, b)
+    x1, it1, dj1, db1 = pcg.pcg(S.A_ff, b, x0, S.pinv_f, 1e-10, resid_period=7)
+    lo, hi = precond.chebyshev_interval(precond.element_lam_max(p), 10.0)
+    # degree 1 scales P^-1 by a constant, which leaves every CG iterate unchanged
+    xc, itc, djc, dbc = precond.pcg_cheb(S.A_ff, b, x0, S.pinv_f, 1, lo, hi, 1e-10, resid_period=7)
+    assert itc == it1 and dbc == db1
+    assert np.linalg.norm(xc - x1) <= 1e-12 * np.linalg.norm(x1)
+    its = [itc]
+    for m in (2, 3, 4):
+        x, it, dj, _ = precond.pcg_cheb(S.A_ff, b, x0, S.pinv_f, m, lo, hi, 1e-10, resid_period=7)
+        assert dj <= 1e-20 * dbc
+        assert np.linalg.norm(x - exact) <= 1e-8 * np.linalg.norm(exact)
+        its.append(it)
+    assert all(a > b for a, b in zip(its, its[1:])), its

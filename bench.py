@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--layered-steps", type=int, default=10,
                     help="200^3 layered cube: time steps of its FP32-refined and FP64 legs (0: skip)")
     ap.add_argument("--layered-only", action="store_true", help="run only the 200^3 layered legs")
+    ap.add_argument("--cheb-degrees", default="2,3",
+                    help="Chebyshev-Jacobi degrees timed on the layered FP32-refined leg ('' to skip)")
+    ap.add_argument("--cheb-ratio", type=float, default=10.0, help="Chebyshev interval ratio lam_hi / lam_lo")
     ap.add_argument("--mh-chains", type=int, default=32,
                     help="corrosion inverse problem: Metropolis-Hastings chains solved as one batch (0: skip)")
     ap.add_argument("--mh-iters", type=int, default=8)
@@ -84,8 +87,33 @@ def cpu_worker(nsteps_sample: int):
     res = transient.run(p, solver="pcg", nsteps=nsteps_sample, system=S)
     dt = time.perf_counter() - t0
     it = sum(res.iters)
-    print(json.dumps({"seconds": dt, "iters": it, "dof": p.n_nodes, "steps": nsteps_sample,
-                      "value": p.n_nodes * it / dt}))
+    out = {"seconds": dt, "iters": it, "dof": p.n_nodes, "steps": nsteps_sample, "value": p.n_nodes * it / dt}
+    out["incomplete_factorisation"] = ilu_context()
+    print(json.dumps(out))
+
+
+def ilu_context(n: int = 40):
+    """The paper's CPU comparison solver, PCG with an incomplete factorisation
+    of drop tolerance 1e-3 (SuperLU's ILU standing in for incomplete
+    Cholesky), against the oracle's Jacobi-PCG on the first step of the
+    inclusions workload at n^3 elements (context only, one thread)."""
+    from oracle import pcg, precond, transient
+    import workloads as W
+
+    p = W.inclusions_cube(n=n)
+    S = transient.build_system(p)
+    b = transient.step_rhs(p, S, p.u0, 1)
+    x0 = p.u0[S.free]
+    t0 = time.perf_counter()
+    M = precond.ilu_preconditioner(S.A_ff, drop_tol=1e-3)
+    t1 = time.perf_counter()
+    _, it_ilu = precond.pcg_precond(S.A_ff, b, x0, M, p.rtol)
+    t2 = time.perf_counter()
+    _, it_jac, _, _ = pcg.pcg(S.A_ff, b, x0, S.pinv_f, p.rtol)
+    t3 = time.perf_counter()
+    return {"sample": f"inclusions_cube_{n} ({p.n_nodes} DOF), step 1, rtol {p.rtol:g}", "drop_tol": 1e-3,
+            "factorisation_s": t1 - t0, "ilu_pcg": {"iterations": it_ilu, "solve_s": t2 - t1},
+            "jacobi_pcg": {"iterations": it_jac, "solve_s": t3 - t2}, "cores": 1}
 
 
 def run_cpu_baseline(nsteps_sample: int):
@@ -152,6 +180,10 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+
+def cheb_degrees(args):
+    return tuple(int(x) for x in args.cheb_degrees.split(",") if x.strip())
+
 
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -328,11 +360,13 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tunin
             s.close()
 
 
-def run_layered(hg, torch, nsteps: int, stream, tune=True):
+def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb_ratio=10.0):
     """The 200^3 layered cube (8,120,601 DOF, k 1:1000 layers and 0.01 pockets,
     Dirichlet 1 on z=0, dt=5e-4, theta=0.5, rtol 1e-10): its first `nsteps`
     steps in FP32-refined and in FP64, timed with CUDA events, plus the
-    dominant kernel of each timed alone after an L2 flush."""
+    dominant kernel of each timed alone after an L2 flush; then the same
+    FP32-refined steps with the Chebyshev-Jacobi preconditioner of each
+    degree in cheb_degrees."""
     import numpy as np
     import workloads as W
     p = W.layered_cube(nsteps=nsteps)
@@ -340,8 +374,11 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True):
     peak, _ = measured_peaks()
     out = {"workload": f"layered_cube_200 (8,120,601 DOF), first {nsteps} of its 100 steps, dt=5e-4, theta=0.5, rtol 1e-10"}
     fields = {}
+    tuned32 = None
     for precision in ("fp32_refined", "fp64"):
         tuning = autotune(hg, p, precision, stream) if tune else None
+        if precision == "fp32_refined":
+            tuned32 = tuning
         with hg.Simulation.from_problem(p, precision=precision, stream=stream.cuda_stream) as s:
             s.step(1)  # warm-up (graph capture)
             hg.heat_set_state(s.sim, p.u0, s.n_nodes)
@@ -369,6 +406,35 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True):
                                      if prof["ms_update"] > 0 else None}}
     u32, u64 = fields["fp32_refined"], fields["fp64"]
     out["final_field_rel_err_fp32_refined_vs_fp64"] = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
+    if cheb_degrees:
+        # Chebyshev-Jacobi against the FP32-refined Jacobi leg, same steps and
+        # kernel table (a fused variant gives way to its register-prefetch form)
+        if tuned32 is not None:
+            hg.heat_tuning_set(tuned32["table"]["variant"], tuned32["table"]["seg_nodes"], tuned32["table"]["pw_quads"])
+        jac = out["fp32_refined"]
+        legs = {}
+        for m in cheb_degrees:
+            with hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream,
+                                            cheb_degree=m, cheb_ratio=cheb_ratio) as s:
+                s.step(1)
+                hg.heat_set_state(s.sim, p.u0, s.n_nodes)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st = s.step(nsteps)
+                e.record(stream)
+                e.synchronize()
+                sec = a.elapsed_time(e) / 1e3
+                lo, hi = hg.heat_cheb_interval(s.sim)
+                uc = s.state()
+            legs[f"degree_{m}"] = {"ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
+                                   "iterations_vs_jacobi": st["iters"] / jac["cg_iterations"],
+                                   "operator_passes_vs_jacobi": st["iters"] * m / jac["cg_iterations"],
+                                   "time_vs_jacobi": sec * 1e3 / nsteps / jac["ms_per_step"],
+                                   "interval": [lo, hi], "status": st["status"],
+                                   "final_field_rel_diff_vs_jacobi": float(np.linalg.norm(uc - u32) / np.linalg.norm(u32))}
+        out["chebyshev_fp32_refined"] = {"ratio": cheb_ratio, **legs}
     return out
 
 
@@ -482,7 +548,8 @@ def main():
             t = json.loads(args.tuning_json)
             hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
         print(json.dumps({"layered": run_layered(hg, torch, args.layered_steps, stream,
-                                                 not (args.no_autotune or args.tuning_json))}), flush=True)
+                                                 not (args.no_autotune or args.tuning_json),
+                                                 cheb_degrees(args), args.cheb_ratio)}), flush=True)
         return
     if args.batch_only:  # the batched workload alone (used for profiling captures)
         fixed = bool(args.tuning_json)
@@ -588,7 +655,8 @@ def main():
     if rank == 0 and args.batch_sims > 0:
         batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
     if rank == 0 and args.layered_steps > 0:
-        layered = run_layered(hg, torch, args.layered_steps, stream, not (args.no_autotune or fixed))
+        layered = run_layered(hg, torch, args.layered_steps, stream, not (args.no_autotune or fixed),
+                              cheb_degrees(args), args.cheb_ratio)
     if rank == 0 and args.mh_chains > 0:
         mh = run_mh(hg, torch, args.mh_chains, args.mh_iters, stream)
     if rank == 0 and args.serve_requests > 0:
@@ -625,7 +693,8 @@ def main():
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"oracle Jacobi-PCG, first {cpu['steps']} time steps of the same workload ({cpu['iters']} CG iterations, {cpu['seconds']:.1f} s; CSR assembly untimed)"}
+                                    "sample": f"oracle Jacobi-PCG, first {cpu['steps']} time steps of the same workload ({cpu['iters']} CG iterations, {cpu['seconds']:.1f} s; CSR assembly untimed)",
+                                    "incomplete_factorisation_context": cpu.get("incomplete_factorisation")}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:

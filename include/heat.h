@@ -75,12 +75,24 @@ typedef struct {
   int poll_period;   /* CG iterations queued between host polls      [32] */
   int precision;     /* heat_precision                               [HEAT_FP64] */
   double inner_rtol; /* FP32_REFINED: inner solve tolerance relative
-                        to its own right-hand side                   [1e-4] */
+                        to its own right-hand side                   [1e-5] */
   int max_outer;     /* FP32_REFINED: refinement sweeps per step     [40] */
   int inner_max_iter; /* FP32_REFINED: CG iterations per inner solve;
                          a restart loses the Krylov space, so stiff
                          systems want long inner solves, >= 1        [2000] */
+  int cheb_degree;   /* preconditioner: 0 or 1 the Jacobi diagonal of
+                        Algorithm 1; m in [2, HEAT_CHEB_MAX_DEGREE]
+                        the Chebyshev polynomial z = p_m(D^-1 A) D^-1 r
+                        (m - 1 extra operator passes per CG iteration,
+                        fewer iterations). The stopping test stays
+                        r^T P^-1 r of Algorithm 1. The FP32 fused
+                        iteration kernels are not used with it.      [0] */
+  double cheb_ratio; /* Chebyshev interval [lam_hi / ratio, lam_hi] of
+                        D^-1 A, lam_hi an element-wise Gershgorin bound
+                        (see heat_cheb_interval), > 1                [10] */
 } heat_params;
+
+#define HEAT_CHEB_MAX_DEGREE 8
 
 /* Boundary conditions (§3.1 strong form: k dT/dn = f on the sides). */
 typedef struct {
@@ -132,8 +144,17 @@ heat_status heat_set_coeffs(heat_sim* sim, const double* rho_c, const double* k,
  * host or device buffers). Returns after the copy. */
 heat_status heat_get_coeffs(heat_sim* sim, double* rho_c, double* k, int on_device);
 
-/* Change dt / theta / tolerances / precision between steps. */
+/* Change dt / theta / tolerances / precision / preconditioner between steps. */
 heat_status heat_set_params(heat_sim* sim, const heat_params* params);
+
+/* The interval [lam_lo, lam_hi] of the Chebyshev preconditioner (params
+ * cheb_degree >= 2): lam_hi = max over elements e of
+ * sum_p |rho_c_e Mhat[p] / dt + theta k_e Khat[p]| / (rho_c_e Mhat[0] / dt +
+ * theta k_e Khat[0]), the element-wise Gershgorin bound of the spectrum of
+ * D^-1 A (Mhat, Khat: the rows of the Q1 element matrices of §3.2), and
+ * lam_lo = lam_hi / cheb_ratio. Recomputed whenever the coefficients or the
+ * parameters change. HEAT_ERR_ARG when the preconditioner is off. */
+heat_status heat_cheb_interval(heat_sim* sim, double* lam_lo, double* lam_hi);
 
 /* Set the current temperature U (N values, node order) and restart the time
  * history (the next step extrapolates from U alone). Dirichlet nodes are

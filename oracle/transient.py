@@ -14,7 +14,7 @@ from typing import List
 
 import numpy as np
 
-from . import fem, pcg as _pcg
+from . import fem, pcg as _pcg, precond as _precond
 
 
 @dataclass
@@ -73,8 +73,10 @@ class Result:
 
 
 def run(p, solver: str = "direct", rtol: float = None, max_iter: int = 20000,
-        nsteps: int = None, system: System = None, callback=None) -> Result:
-    """Run the transient; solver is 'direct' (sparse LU), 'dense' or 'pcg'."""
+        nsteps: int = None, system: System = None, callback=None, cheb=None) -> Result:
+    """Run the transient; solver is 'direct' (sparse LU), 'dense' or 'pcg'
+    (Algorithm 1; with cheb = (degree, ratio) its Chebyshev-preconditioned
+    form on the interval [lam_hi / ratio, lam_hi] of the element bound)."""
     S = system or build_system(p)
     rtol = p.rtol if rtol is None else rtol
     nsteps = p.nsteps if nsteps is None else nsteps
@@ -88,7 +90,11 @@ def run(p, solver: str = "direct", rtol: float = None, max_iter: int = 20000,
     res = Result(u=[u_prev.copy()])
     for n in range(1, nsteps + 1):
         b_f = step_rhs(p, S, u_prev, n)
-        if solver == "pcg":
+        if solver == "pcg" and cheb is not None:
+            x0 = u_prev if u_prev2 is None else 2.0 * u_prev - u_prev2
+            lo, hi = _precond.chebyshev_interval(_precond.element_lam_max(p), cheb[1])
+            x, it, _, _ = _precond.pcg_cheb(S.A_ff, b_f, x0[S.free], S.pinv_f, cheb[0], lo, hi, rtol, max_iter)
+        elif solver == "pcg":
             x0 = u_prev if u_prev2 is None else 2.0 * u_prev - u_prev2
             x, it, _, _ = _pcg.pcg(S.A_ff, b_f, x0[S.free], S.pinv_f, rtol, max_iter)
         elif solver == "dense":

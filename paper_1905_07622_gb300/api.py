@@ -42,7 +42,7 @@ class heat_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("dt", C.c_double), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("resid_period", C.c_int), ("poll_period", C.c_int),
                 ("precision", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
-                ("inner_max_iter", C.c_int)]
+                ("inner_max_iter", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double)]
 
 
 class heat_bc(C.Structure):
@@ -145,6 +145,7 @@ _SIGS = [
     ("heat_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
     ("heat_batch_autotune", C.c_int, [_VP, C.c_int, C.POINTER(heat_tuning), _DP]),
     ("heat_get_coeffs", C.c_int, [_VP, _VP, _VP, C.c_int]),
+    ("heat_cheb_interval", C.c_int, [_VP, _DP, _DP]),
     ("heat_set_face_flux", C.c_int, [_VP, C.c_int, _VP, C.c_int]),
     ("heat_set_coeffs_corrosion", C.c_int, [_VP, C.POINTER(heat_corrosion), C.c_double]),
     ("heat_face_loglik", C.c_int, [_VP, C.c_int, _VP, C.c_double, _VP]),
@@ -554,6 +555,13 @@ def heat_get_coeffs(sim, n_elems: int):
     kk = np.empty(n_elems)
     _check(_lib.heat_get_coeffs(sim, C.c_void_p(rc.ctypes.data), C.c_void_p(kk.ctypes.data), 0))
     return rc, kk
+
+
+def heat_cheb_interval(sim):
+    """(lam_lo, lam_hi) of the Chebyshev preconditioner (cheb_degree >= 2)."""
+    lo, hi = C.c_double(), C.c_double()
+    _check(_lib.heat_cheb_interval(sim, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
 
 
 def heat_set_coeffs_corrosion(sim, geom: heat_corrosion, depth: float):

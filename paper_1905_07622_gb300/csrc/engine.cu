@@ -31,13 +31,17 @@ struct KernelSet {
   int seg_nodes[3];  // warp-segment tile size per mesh-size bucket
   int apply_w_smem;  // dynamic shared memory of apply_w per block
   bool fused;        // apply_w is k_cg_iter: one kernel per CG iteration, no update kernel
+  // Chebyshev passes: block form, and the warp form matching apply_w (which
+  // then replaces it, on the same work list)
+  TileFn cheb, cheb_w;
 };
 
 template <int P, int SX, int SY>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
   return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P, sizeof(T) == 4 ? 4 : 2>, SX, SY, SX * SY,
-          SX * SY, nullptr, 0, 0, 0, pw_chunk(sizeof(T) == 4 ? 4 : 2), {512, 512, 512}, 0, false};
+          SX * SY, nullptr, 0, 0, 0, pw_chunk(sizeof(T) == 4 ? 4 : 2), {512, 512, 512}, 0, false,
+          k_cheb<T, SX, SY>, nullptr};
 }
 
 // Warp-segment apply variants the tuner chooses from: segment width, rows per
@@ -48,7 +52,21 @@ struct WVariant {
   TileFn f32, f64;
   int smem32, smem64;  // dynamic shared memory per block
   bool fused;          // FP32 only: the fused iteration kernel k_cg_iter
+  TileFn cheb32, cheb64;  // Chebyshev passes of this segment shape (null: fused)
 };
+// One register-prefetch Chebyshev pass kernel per segment shape and type,
+// bounded like that shape's register-prefetch apply (FP64: one block per SM).
+template <class T, int SX, int NY, int W, bool ON>
+static constexpr TileFn chebfn() {
+  if constexpr (!ON) {
+    return nullptr;
+  } else if constexpr (sizeof(T) == 8) {
+    return k_cheb_w<double, SX, NY, W, 1>;
+  } else {
+    constexpr int MINB = (SX == 16 && NY == 2) ? 2 : ((SX == 32 && NY == 2) ? 4 : 3);
+    return k_cheb_w<float, SX, NY, W, MINB>;
+  }
+}
 template <class T, int SX, int NY, int W, int S, int MINB, bool ON>
 static constexpr TileFn wfn() {
   if constexpr (ON) return k_apply_dot_w<T, SX, NY, W, S, MINB>;
@@ -58,11 +76,12 @@ template <int SX, int NY, int W, int S, int MINB, int MINB64>
 static constexpr WVariant wv() {
   return {SX, NY, W, S, wfn<float, SX, NY, W, S, MINB, true>(), wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0)>(),
           S ? 32 * W * async_stage_bytes<float, NY, (S ? S : 2)>() : 0,
-          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0, false};
+          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0, false, chebfn<float, SX, NY, W, true>(),
+          chebfn<double, SX, NY, W, (MINB64 > 0)>()};
 }
 template <int SX, int NY, int W, int MINB>
 static constexpr WVariant wv_fused() {
-  return {SX, NY, W, 0, k_cg_iter<SX, NY, W, MINB>, nullptr, 0, 0, true};
+  return {SX, NY, W, 0, k_cg_iter<SX, NY, W, MINB>, nullptr, 0, 0, true, nullptr, nullptr};
 }
 // (segment width, rows, warps, stages, min blocks per SM for float / double,
 // 0 = no double kernel)
@@ -130,8 +149,20 @@ static TileFn update_kernel(int prec, int qpt) {
   }
 }
 
-static KernelSet kernel_set(int prec, const Tuning& t) {
-  const int variant = t.variant[prec];
+// The kernels of precision prec under tuning table t. With Chebyshev passes
+// (cheb) a fused variant is replaced by the register-prefetch variant of the
+// same segment shape: the fused iteration has no place for the passes.
+static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false) {
+  int variant = t.variant[prec];
+  if (cheb && variant >= 0 && variant < kNumVariants && kVariants[variant].fused) {
+    const WVariant& f = kVariants[variant];
+    int alt = -1;
+    for (int v = 0; v < kNumVariants && alt < 0; ++v)
+      if (!kVariants[v].fused && kVariants[v].stages == 0 && kVariants[v].sx == f.sx && kVariants[v].ny == f.ny &&
+          kVariants[v].warps == f.warps)
+        alt = v;
+    variant = alt >= 0 ? alt : 0;
+  }
   KernelSet k = prec == P_FP64 ? make_set<P_FP64, 16, 16>()
                                : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16>()
                                                           : make_set<P_FP32_PLAIN, 16, 16>());
@@ -144,6 +175,7 @@ static KernelSet kernel_set(int prec, const Tuning& t) {
       k.wwarps = v.warps;
       k.apply_w_smem = prec == P_FP64 ? v.smem64 : v.smem32;
       k.fused = v.fused;
+      k.cheb_w = prec == P_FP64 ? v.cheb64 : v.cheb32;
       if (k.apply_w_smem > 0)
         cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
     }
@@ -191,6 +223,8 @@ struct Engine {
   double* d_partial = nullptr;
   long long cap_op = 0, cap_pw = 0, cap_partial = 0;
   int grid_op = 0, grid_pw = 0, iters_per_tick = 4;
+  int ncheb = 0;    // Chebyshev passes per iteration in the tick: max over members of degree - 1
+  int grid_ch = 0;  // grid of the pass kernel
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long launches = 0;  // kernels launched by the last engine_step_all
@@ -201,8 +235,18 @@ struct Engine {
   std::vector<int2> h_op, h_pw;
 };
 
-// Kernels in one tick: k_open, then per iteration apply + update, or the fused kernel.
-static int tick_launches(const Engine* e) { return 1 + (e->ks.fused ? 1 : 2) * e->iters_per_tick; }
+// Kernels in one tick: k_open, then per iteration the Chebyshev passes and
+// apply + update, or the fused kernel.
+static int tick_launches(const Engine* e) {
+  return 1 + (e->ncheb + (e->ks.fused ? 1 : 2)) * e->iters_per_tick;
+}
+
+// Chebyshev passes the members need per iteration.
+static int members_ncheb(const Engine* e) {
+  int n = 0;
+  for (const heat_sim* s : e->sims) n = std::max(n, s->dev.cheb_m >= 2 ? s->dev.cheb_m - 1 : 0);
+  return n;
+}
 
 // Operator tile geometry of one simulation: (SX-1) x (SY-1) node columns per
 // tile, tz_len levels. tz_len trades z-halo work (3 extra levels per tile)
@@ -283,9 +327,16 @@ static heat_status engine_upload(Engine* e) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pw, e->ks.update, kPwThreads, 0);
   if (e->ks.apply_w)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_aw, e->ks.apply_w, 32 * e->ks.wwarps, e->ks.apply_w_smem);
+  int occ_ch = 1;
+  if (e->ks.cheb_w)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ch, e->ks.cheb_w, 32 * e->ks.wwarps, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ch, e->ks.cheb, e->ks.apply_threads, 0);
   e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
   e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
   e->grid_aw = (int)std::max(1LL, std::min<long long>(nwork[2], (long long)sms * std::max(1, occ_aw)));
+  e->grid_ch = (int)std::max(1LL, std::min<long long>(e->ks.cheb_w ? nwork[2] : nwork[0],
+                                                      (long long)sms * std::max(1, occ_ch)));
   return HEAT_OK;
 }
 
@@ -347,6 +398,11 @@ static heat_status engine_capture(Engine* e) {
   if (err == cudaSuccess) {
     cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
     for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
+      for (int k = 0; k < e->ncheb && lerr == cudaSuccess; ++k) {
+        if (e->ks.cheb_w) lerr = launch(e->ks.cheb_w, e->grid_ch, 32 * e->ks.wwarps, e->d_work_aw, e->d_nwork + 2, 0);
+        else lerr = launch(e->ks.cheb, e->grid_ch, e->ks.apply_threads, e->d_work_op, e->d_nwork, 0);
+      }
+      if (lerr != cudaSuccess) break;
       lerr = launch(afn, agrid, athreads, awork, anwork, asmem);
       if (lerr == cudaSuccess && !e->ks.fused)
         lerr = launch(e->ks.update, e->grid_pw, kPwThreads, e->d_work_pw, e->d_nwork + 1, 0);
@@ -370,7 +426,8 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   Engine* e = new Engine();
   e->sims.assign(sims, sims + nsims);
   e->prec = precision;
-  e->ks = kernel_set(precision, tun ? *tun : tuning_get());
+  e->ncheb = members_ncheb(e);
+  e->ks = kernel_set(precision, tun ? *tun : tuning_get(), e->ncheb > 0);
   e->stream = stream;
   // capacities: the geometry is a function of each mesh, so compute it
   long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_partial = 0;
@@ -441,10 +498,25 @@ void engine_destroy(Engine* e) {
 }
 
 heat_status engine_refresh(Engine* e) {
-  const int g_op = e->grid_op, g_pw = e->grid_pw, g_aw = e->grid_aw;
+  const int g_op = e->grid_op, g_pw = e->grid_pw, g_aw = e->grid_aw, g_ch = e->grid_ch;
+  // a member's preconditioner may have changed: the passes per iteration, and
+  // with them the kernel set (no fused iteration with passes) and the graph
+  const int nch = members_ncheb(e);
+  const bool recapture = nch != e->ncheb;
+  if ((nch > 0) != (e->ncheb > 0)) {
+    const KernelSet ks = kernel_set(e->prec, tuning_get(), nch > 0);
+    bool same_shape = ks.wsx == e->ks.wsx && ks.wny == e->ks.wny && ks.wwarps == e->ks.wwarps &&
+                      ks.pw_chunk == e->ks.pw_chunk && (ks.apply_w != nullptr) == (e->ks.apply_w != nullptr);
+    for (int b = 0; b < 3; ++b) same_shape = same_shape && ks.seg_nodes[b] == e->ks.seg_nodes[b];
+    if (!same_shape)  // the work lists were sized for the old shape
+      return set_error(HEAT_ERR_ARG, "engine: the tuning table changed since the engine was built; rebuild it");
+    e->ks = ks;
+  }
+  e->ncheb = nch;
   heat_status st = engine_upload(e);
   if (st != HEAT_OK) return st;
-  if (!e->gexec || e->grid_op != g_op || e->grid_pw != g_pw || e->grid_aw != g_aw) return engine_capture(e);
+  if (recapture || !e->gexec || e->grid_op != g_op || e->grid_pw != g_pw || e->grid_aw != g_aw || e->grid_ch != g_ch)
+    return engine_capture(e);
   return HEAT_OK;
 }
 
@@ -605,6 +677,8 @@ __global__ void k_profile_seed(T* __restrict__ r, const T* __restrict__ pinv, lo
 // (a converged step leaves a residual near underflow).
 static heat_status profile_arm(Engine* e, double* d_delta, std::vector<double>& h_delta) {
   heat_status st = HEAT_OK;
+  if (e->ncheb > 0)
+    return set_error(HEAT_ERR_ARG, "profiling and tuning time the Jacobi iteration: set cheb_degree to 0 for them");
   if (cudaMemsetAsync(d_delta, 0, sizeof(double) * e->sims.size(), e->stream) != cudaSuccess)
     return set_error(HEAT_ERR_CUDA, "profile: memset failed");
   for (size_t i = 0; i < e->sims.size(); ++i) {

@@ -59,6 +59,8 @@ extern "C" void heat_params_default(heat_params* p) {
   p->inner_rtol = 1e-5;
   p->max_outer = 40;
   p->inner_max_iter = 2000;
+  p->cheb_degree = 0;
+  p->cheb_ratio = 10.0;
 }
 
 extern "C" heat_status heat_create_mesh(int nx, int ny, int nz, const double origin[3],
@@ -170,6 +172,10 @@ static heat_status check_params(const heat_params* p) {
     if (p->max_outer < 1) return set_error(HEAT_ERR_ARG, "max_outer must be >= 1");
     if (p->inner_max_iter < 1) return set_error(HEAT_ERR_ARG, "inner_max_iter must be >= 1");
   }
+  if (p->cheb_degree < 0 || p->cheb_degree > HEAT_CHEB_MAX_DEGREE)
+    return set_error(HEAT_ERR_ARG, "cheb_degree must be in [0, %d] (got %d)", HEAT_CHEB_MAX_DEGREE, p->cheb_degree);
+  if (p->cheb_degree >= 2 && !(p->cheb_ratio > 1.0 && std::isfinite(p->cheb_ratio)))
+    return set_error(HEAT_ERR_ARG, "cheb_ratio must be finite and > 1 (got %g)", p->cheb_ratio);
   return HEAT_OK;
 }
 
@@ -183,6 +189,7 @@ static void fill_params(heat_sim* s) {
   d.resid_period = s->prm.resid_period;
   d.max_outer = s->prm.max_outer;
   d.inner_max_iter = s->prm.inner_max_iter;
+  d.cheb_m = s->prm.cheb_degree >= 2 ? s->prm.cheb_degree : 0;  // degree 1 is Jacobi scaled by a constant
   d.prec = s->prm.precision;
 }
 
@@ -202,6 +209,16 @@ heat_status heat::sim_setup_flux(heat_sim* s) {
   return HEAT_OK;
 }
 
+// Interval and coefficients of the Chebyshev preconditioner (when it is on).
+static heat_status sim_setup_cheb(heat_sim* s) {
+  if (s->dev.cheb_m < 2) return HEAT_OK;
+  CUDA_TRY(cudaMemsetAsync(s->dev.cheb + 18, 0, sizeof(double), s->stream));
+  k_cheb_bound<<<grid_for(s->ne, 256), 256, 0, s->stream>>>(s->d_dev);
+  k_cheb_coef<<<1, 1, 0, s->stream>>>(s->d_dev, s->dev.cheb_m, s->prm.cheb_ratio);
+  CUDA_TRY(cudaGetLastError());
+  return HEAT_OK;
+}
+
 heat_status heat::sim_derive_async(heat_sim* s) {
   const int g = grid_for(s->nn, 256);
   CUDA_TRY(cudaMemsetAsync(&s->d_sc->y_valid, 0, sizeof(int), s->stream));
@@ -210,7 +227,7 @@ heat_status heat::sim_derive_async(heat_sim* s) {
   k_setup_diag<<<g, 256, 0, s->stream>>>(s->d_dev);
   k_setup_lift<<<g, 256, 0, s->stream>>>(s->d_dev);
   CUDA_TRY(cudaGetLastError());
-  return HEAT_OK;
+  return sim_setup_cheb(s);
 }
 
 static heat_status sim_refresh(heat_sim* s) {
@@ -224,6 +241,8 @@ static heat_status sim_refresh(heat_sim* s) {
   k_setup_diag<<<g, 256, 0, s->stream>>>(s->d_dev);
   k_setup_lift<<<g, 256, 0, s->stream>>>(s->d_dev);
   CUDA_TRY(cudaGetLastError());
+  st = sim_setup_cheb(s);
+  if (st != HEAT_OK) return st;
   unsigned int bad = 0;
   CUDA_TRY(cudaMemcpyAsync(&bad, s->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -325,6 +344,8 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   ALLOC(d.rc32[1], N4, float*);
   ALLOC(d.wc32[1], N4, float*);
   ALLOC(d.p32, N4, float*);
+  ALLOC(d.z32, N4, float*);
+  ALLOC(d.cheb, sizeof(double) * 20, double*);
   d.rc32[0] = d.r32;
   d.wc32[0] = d.q32;
   d.sc32[0] = d.d32[0];
@@ -360,6 +381,8 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
         cudaMemsetAsync(d.p32, 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.rc32[1], 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.wc32[1], 0, N4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d.z32, 0, N4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d.cheb, 0, sizeof(double) * 20, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->d_q6, b.flux, sizeof(double) * 6, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
       st = set_error(HEAT_ERR_CUDA, "heat_sim_create: initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
       goto fail;
@@ -453,6 +476,17 @@ extern "C" heat_status heat_set_params(heat_sim* s, const heat_params* params) {
   st = sim_refresh(s);
   if (st != HEAT_OK) return st;
   if (s->eng) return engine_refresh(s->eng);
+  return HEAT_OK;
+}
+
+extern "C" heat_status heat_cheb_interval(heat_sim* s, double* lam_lo, double* lam_hi) {
+  if (!s || !lam_lo || !lam_hi) return set_error(HEAT_ERR_ARG, "heat_cheb_interval: null argument");
+  if (s->dev.cheb_m < 2) return set_error(HEAT_ERR_ARG, "heat_cheb_interval: the Chebyshev preconditioner is off");
+  double v[2];
+  CUDA_TRY(cudaMemcpyAsync(v, s->dev.cheb + 16, sizeof(v), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  *lam_lo = v[0];
+  *lam_hi = v[1];
   return HEAT_OK;
 }
 
@@ -562,8 +596,8 @@ heat_status heat::sim_prepare_steps(heat_sim* s, int nsteps) {
 }
 
 size_t heat::sim_footprint(long long nn, long long ne) {
-  // 16 FP64 and 9 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
-  return (size_t)nn * (16 * 8 + 9 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
+  // 16 FP64 and 10 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
+  return (size_t)nn * (16 * 8 + 10 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
          4096 * sizeof(int) + 1024;
 }
 

@@ -17,7 +17,8 @@ enum Phase : int {
   PH_OUTER = 3,   // FP32 path: x64 += e, FP64 true residual, restart inner
   PH_DONE = 4,    // target step reached
   PH_FAILED = 5,  // status holds the error
-  PH_RESID = 6    // FP64 path: true residual r = b - A x (every resid_period iterations)
+  PH_RESID = 6,   // FP64 path: true residual r = b - A x (every resid_period iterations)
+  PH_CHEB = 7     // Chebyshev preconditioner z = p_m(D^-1 A) D^-1 r, one operator pass per kernel
 };
 
 enum Prec : int { P_FP64 = 0, P_FP32_REFINED = 1, P_FP32_PLAIN = 2 };
@@ -44,6 +45,8 @@ struct SimScalars {
   unsigned int count;  // tiles finished in the running kernel
   int cgs;             // FP32 fused iteration: current slot of r, w, s (0/1)
   int y_valid;         // bit v: yv[v] holds A' vec64[v] (FP32 paths, see k_open)
+  int cheb_k;          // next Chebyshev pass (1 .. cheb_m - 1) while phase is PH_CHEB
+  int pad_sc_;
   unsigned int check_violations;  // out-of-range indices met (HEAT_CHECK builds)
   double delta;    // r^T P^-1 r of the current solve
   double delta_b;  // b^T P^-1 b of the step
@@ -71,7 +74,8 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   uint32_t dir_faces;         // Dirichlet face bits
   int prec;                   // Prec
   int max_iter, resid_period, max_outer, flux_steps;
-  int inner_max_iter, pad_prm_;
+  int inner_max_iter;
+  int cheb_m;                 // Chebyshev preconditioner degree (>= 2), 0: Jacobi (Algorithm 1)
   double g[6];                // Dirichlet values
   double inv_dt, theta, rtol, inner_rtol;
   double mhat[8], khat[8];    // element mass/stiffness entry by corner XOR pattern
@@ -105,6 +109,15 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   float* wc32[2];
   float* sc32[2];
   float* p32;
+  // Chebyshev preconditioner (cheb_m >= 2): z, the polynomial's residual res
+  // and its two step vectors dd. FP32: z32, rc32[1], wc32[1], p32 (the fused
+  // iteration's slots, idle on the non-fused kernels the preconditioner runs
+  // with); FP64: yv[0..3] (the stored products are an FP32-path device).
+  float* z32;
+  // [0] 1/theta, [2k-1], [2k] the step-k coefficients rho_k rho_{k-1} and
+  // 2 rho_k / delta (k = 1..7), [16] lam_lo, [17] lam_hi, [18] the bound's
+  // running maximum as bits (see k_cheb_bound)
+  double* cheb;
   double* partial;            // 2 per tile
   int* iters_log;             // CG iterations of each step
   int iters_log_len;

@@ -34,6 +34,52 @@ __global__ void k_setup_diag(const SimDev* __restrict__ sp) {
   }
 }
 
+// Upper bound of the spectrum of D^-1 A for the Chebyshev preconditioner
+// (Gershgorin, element by element): a node's absolute row sum is at most the
+// sum over its elements of the element rows' absolute sums, and a ratio of
+// sums of positive terms is at most the largest ratio of terms, so
+//   lam_max <= max_e sum_p |a_e Mhat[p] + b_e Khat[p]| / (a_e Mhat[0] + b_e Khat[0]),
+// a_e = rho_c_e / dt, b_e = theta k_e (every corner of a box element has the
+// same row, indexed by the corner XOR pattern p). The maximum is taken on the
+// bit patterns of the non-negative doubles (ordered like the values) in
+// s.cheb[18], which the caller zeroes first; it does not depend on the order.
+__global__ void k_cheb_bound(const SimDev* __restrict__ sp) {
+  const SimDev& s = *sp;
+  const long long ne = (long long)s.nx * s.ny * s.nz;
+  double best = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 cf = s.coef[e];
+    const double a = s.inv_dt * cf.x, b = s.theta * cf.y;
+    double row = 0.0;
+    for (int p = 0; p < 8; ++p) row += fabs(a * s.mhat[p] + b * s.khat[p]);
+    best = fmax(best, row / (a * s.mhat[0] + b * s.khat[0]));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&s.cheb[18]), (unsigned long long)__double_as_longlong(best));
+}
+
+// Coefficients of the Chebyshev passes (see k_cheb) for degree m and the
+// interval [lam_hi / ratio, lam_hi]. One thread.
+__global__ void k_cheb_coef(const SimDev* __restrict__ sp, int m, double ratio) {
+  const SimDev& s = *sp;
+  double* c = s.cheb;
+  const double hi = __longlong_as_double((long long)*reinterpret_cast<const unsigned long long*>(&c[18]));
+  const double lo = hi / ratio;
+  const double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sigma = th / de;
+  double rho = 1.0 / sigma;
+  c[0] = 1.0 / th;
+  for (int k = 1; k < m; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c[2 * k - 1] = rn * rho;
+    c[2 * k] = 2.0 * rn / de;
+    rho = rn;
+  }
+  c[16] = lo;
+  c[17] = hi;
+}
+
 // Per-element flux densities of the faces that have them (NULL: the face's
 // uniform value applies).
 struct FaceFlux {

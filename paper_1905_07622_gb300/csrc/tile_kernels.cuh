@@ -10,6 +10,9 @@
 //               alpha = delta / d.q.
 //   k_update    [pointwise chunks] x += alpha d, r -= alpha q, delta = r.P^-1 r,
 //               beta, convergence, phase changes, step close.
+//   k_cheb      [operator tiles] with a Chebyshev preconditioner, the m - 1
+//               operator passes of z = p_m(D^-1 A) D^-1 r before each apply
+//               (PH_CHEB); the apply then stages d = z + beta d_old.
 // Every reduction is a per-item partial summed in item order by the last
 // block of the simulation, so a simulation's result does not depend on what
 // else shares the launch.
@@ -39,7 +42,7 @@ __host__ __device__ constexpr int pw_min_blocks(int qpt, int bytes) {
 // Control scalars of a simulation (written only by earlier kernels, or by
 // the last block after all of the simulation's items of this kernel).
 struct Ctl {
-  int phase, iu1, iu2, ix, ixa, id, restart, have_prev, iter, step, cgs, y_valid;
+  int phase, iu1, iu2, ix, ixa, id, restart, have_prev, iter, step, cgs, y_valid, cheb_k;
   double alpha, beta;
 };
 
@@ -57,6 +60,7 @@ __device__ __forceinline__ Ctl load_ctl(const SimScalars* sc) {
   c.step = __ldcg(&sc->step);
   c.cgs = __ldcg(&sc->cgs);
   c.y_valid = __ldcg(&sc->y_valid);
+  c.cheb_k = __ldcg(&sc->cheb_k);
   c.alpha = __ldcg(&sc->alpha);
   c.beta = __ldcg(&sc->beta);
   return c;
@@ -207,6 +211,17 @@ __device__ __forceinline__ void close_step(const SimDev& s, SimScalars* sc, doub
 __device__ __forceinline__ void fail(SimScalars* sc, int status) {
   sc->status = status;
   sc->phase = PH_FAILED;
+}
+
+// The next CG iteration starts: with a Chebyshev preconditioner its passes
+// come first (they set delta = r^T z and beta), otherwise the apply.
+__device__ __forceinline__ void enter_iter(const SimDev& s, SimScalars* sc) {
+  if (s.cheb_m >= 2) {
+    sc->cheb_k = 1;
+    sc->phase = PH_CHEB;
+  } else {
+    sc->phase = PH_ITER;
+  }
 }
 
 struct TileCoords {
@@ -375,14 +390,16 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       sc->count = 0;
       if (phase == PH_RESID) {
         const double dn = tot[0];
-        sc->beta = dn / sc->delta;
-        sc->delta = dn;
+        if (s.cheb_m < 2) {  // a Chebyshev pass forms delta = r^T z and beta instead
+          sc->beta = dn / sc->delta;
+          sc->delta = dn;
+        }
         sc->iter += 1;
         sc->iter_step += 1;
         if (!isfinite(dn)) fail(sc, ST_NONFINITE);
         else if (dn <= sc->thresh) close_step(s, sc, dn);
         else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
-        else sc->phase = PH_ITER;
+        else enter_iter(s, sc);
       } else {
         if (phase == PH_OPEN) {
           sc->delta_b = tot[1];
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
         } else if (P == P_FP64) {
           sc->delta = tot[0];
           if (tot[0] <= sc->thresh) close_step(s, sc, tot[0]);
-          else sc->phase = PH_ITER;
+          else enter_iter(s, sc);
         } else {
           sc->delta_out = tot[0];
           sc->delta = tot[2];
@@ -419,7 +436,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
             // the next sweep's FP64 residual can close the step.
             sc->thresh_in = (P == P_FP32_PLAIN) ? sc->thresh
                                                 : fmax(s.inner_rtol * s.inner_rtol * tot[2], 0.25 * sc->thresh);
-            sc->phase = PH_ITER;
+            enter_iter(s, sc);
           }
         }
       }
@@ -471,6 +488,18 @@ template <> struct IterVecs<float> {
   __device__ static const float2* coef(const SimDev& s) { return s.coef32; }
 };
 
+template <class T> struct ChebVecs;
+template <> struct ChebVecs<double> {
+  __device__ static double* z(const SimDev& s) { return s.yv[0]; }
+  __device__ static double* res(const SimDev& s) { return s.yv[1]; }
+  __device__ static double* dd(const SimDev& s, int k) { return s.yv[2 + k]; }
+};
+template <> struct ChebVecs<float> {
+  __device__ static float* z(const SimDev& s) { return s.z32; }
+  __device__ static float* res(const SimDev& s) { return s.rc32[1]; }
+  __device__ static float* dd(const SimDev& s, int k) { return k ? s.p32 : s.wc32[1]; }
+};
+
 template <class T>
 struct DirRaw {
   T p, r, d;
@@ -494,8 +523,10 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
     if (c.phase != PH_ITER) continue;
     const Geo g(s);
     const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
-    const T* __restrict__ r = IterVecs<T>::r(s);
-    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+    // d = P^-1 r + beta d_old, or z + beta d_old after Chebyshev passes (no scale)
+    const bool ch = s.cheb_m >= 2;
+    const T* __restrict__ r = ch ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);
+    const T* __restrict__ pinv = ch ? nullptr : IterVecs<T>::pinv(s);
     const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
     T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
     T* __restrict__ q = IterVecs<T>::q(s);
@@ -507,7 +538,7 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
         g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
         [&](int m, bool live) -> DirRaw<T> {
           if (!live) return {T(0), T(0), T(0)};
-          return {pinv[m], r[m], rs ? T(0) : dold[m]};
+          return {pinv ? pinv[m] : T(1), r[m], rs ? T(0) : dold[m]};
         },
         [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; },
         [&](int m, bool dir, T y, T v) {
@@ -562,8 +593,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
     const int tile = wi.y * SPC + (int)threadIdx.x / SX;
     const bool active = tile < s.w_ntiles;
     const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
-    const T* __restrict__ r = IterVecs<T>::r(s);
-    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+    const bool ch = s.cheb_m >= 2;  // see k_apply_dot
+    const T* __restrict__ r = ch ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);
+    const T* __restrict__ pinv = ch ? nullptr : IterVecs<T>::pinv(s);
     const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
     T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
     T* __restrict__ q = IterVecs<T>::q(s);
@@ -582,7 +614,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
           (T)s.theta, true,
           [&](int m, bool live) -> DirRaw<T> {
             if (!live) return {T(0), T(0), T(0)};
-            return {pinv[m], r[m], rs ? T(0) : dold[m]};
+            return {pinv ? pinv[m] : T(1), r[m], rs ? T(0) : dold[m]};
           },
           [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
     } else {
@@ -607,6 +639,158 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
         sc->restart = 0;
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ k_cheb
+
+// One pass k (1 <= k <= m-1) of the Chebyshev preconditioner
+// z = p_m(D^-1 A) D^-1 r for the interval [lam_lo, lam_hi] of D^-1 A, the
+// three-term recurrence of the Chebyshev semi-iteration for A z = r started
+// from z = 0 (theta, delta the interval's centre and half-width,
+// sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1})):
+//   dd_0 = D^-1 r / theta,  z_1 = dd_0,  res_0 = r,
+//   res_k = res_{k-1} - A dd_{k-1},
+//   dd_k = rho_k rho_{k-1} dd_{k-1} + (2 rho_k / delta) D^-1 res_k,
+//   z_{k+1} = z_k + dd_k.
+// Pass k stages dd_{k-1} (formed from r on pass 1) through the operator and
+// updates its own nodes; dd_k lives in slot k & 1. The last pass writes only
+// z_m and sums r^T z_m, which becomes delta (and beta = delta / delta_old)
+// of the CG iteration. Dirichlet rows and columns are masked as in the apply.
+template <class T>
+struct ChRaw {
+  T a, b;
+};
+
+template <class T>
+struct ChebPass {
+  const T* __restrict__ r;
+  const T* __restrict__ pinv;
+  const T* __restrict__ ddin;
+  T* __restrict__ ddout;
+  T* __restrict__ res;
+  T* __restrict__ z;
+  T inv_th, c1, c2;
+  bool first, last;
+  T acc;
+
+  __device__ __forceinline__ ChebPass(const SimDev& s, int k) {
+    first = k == 1;
+    last = k == s.cheb_m - 1;
+    r = IterVecs<T>::r(s);
+    pinv = IterVecs<T>::pinv(s);
+    ddin = ChebVecs<T>::dd(s, (k - 1) & 1);
+    ddout = ChebVecs<T>::dd(s, k & 1);
+    res = ChebVecs<T>::res(s);
+    z = ChebVecs<T>::z(s);
+    inv_th = (T)__ldg(&s.cheb[0]);
+    c1 = (T)__ldg(&s.cheb[2 * k - 1]);
+    c2 = (T)__ldg(&s.cheb[2 * k]);
+    acc = T(0);
+  }
+  __device__ __forceinline__ ChRaw<T> fetch(int m, bool live) const {
+    if (!live) return {T(0), T(0)};
+    if (first) return {pinv[m], r[m]};
+    return {ddin[m], T(0)};
+  }
+  __device__ __forceinline__ T value(const ChRaw<T>& v) const { return first ? v.a * v.b * inv_th : v.a; }
+  // v = dd_{k-1} at node m, y = (A dd_{k-1})_m
+  __device__ __forceinline__ void out(int m, bool dir, T y, T v) {
+    if (dir) {
+      z[m] = T(0);
+      return;
+    }
+    const T rr = (first || last) ? r[m] : T(0);
+    const T rk = (first ? rr : res[m]) - y;
+    const T dk = c1 * v + c2 * (pinv[m] * rk);
+    const T zn = (first ? v : z[m]) + dk;
+    z[m] = zn;
+    if (last) {
+      acc += rr * zn;
+    } else {
+      res[m] = rk;
+      ddout[m] = dk;
+    }
+  }
+};
+
+// The last block of a pass: advance to the next pass, or (last pass) set
+// delta = r^T z, beta, and hand the iteration to the apply.
+__device__ __forceinline__ void cheb_close(const SimDev& s, const Ctl& c, double gam) {
+  SimScalars* sc = s.sc;
+  sc->count = 0;
+  if (c.cheb_k < s.cheb_m - 1) {
+    sc->cheb_k = c.cheb_k + 1;
+  } else if (!isfinite(gam)) {
+    fail(sc, ST_NONFINITE);
+  } else if (!(gam > 0.0)) {
+    fail(sc, ST_BREAKDOWN);
+  } else {
+    if (!c.restart) sc->beta = gam / sc->delta;
+    sc->delta = gam;
+    sc->phase = PH_ITER;
+  }
+}
+
+template <class T, int SX, int SY>
+__global__ void __launch_bounds__(SX* SY) k_cheb(const SimDev* __restrict__ sims, const int2* __restrict__ work,
+                                                 const int* __restrict__ nwork_p) {
+  __shared__ TileSmem<T, SX, SY> sh;
+  __shared__ double red[32];
+  __shared__ ItemCache cache;
+  int cur = -1;
+  bool dep = false;
+  allow_next_launch();
+  const int nwork = *nwork_p;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 wi = work[w];
+    cache_sim(sims, wi.x, cache, cur, dep);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    if (c.phase != PH_CHEB) continue;
+    const Geo g(s);
+    const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
+    ChebPass<T> ps(s, c.cheb_k);
+    tile_op<T, SX, SY>(
+        g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
+        [&](int m, bool live) { return ps.fetch(m, live); }, [&](const ChRaw<T>& v) { return ps.value(v); },
+        [&](int m, bool dir, T y, T v) { ps.out(m, dir, y, v); });
+    const T accv[1] = {ps.acc};
+    double tot[1];
+    if (finish_item<T, 1>(s, wi.y, s.ntiles, accv, tot, red)) cheb_close(s, c, tot[0]);
+  }
+}
+
+// Warp-segment form of k_cheb (the register-prefetch march of k_apply_dot_w).
+template <class T, int SX, int NY, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_cheb_w(const SimDev* __restrict__ sims,
+                                                              const int2* __restrict__ work,
+                                                              const int* __restrict__ nwork_p) {
+  constexpr int SPC = WARPS * (32 / SX);  // segments per block
+  __shared__ double red[32];
+  __shared__ ItemCache cache;
+  int cur = -1;
+  bool dep = false;
+  allow_next_launch();
+  const int nwork = *nwork_p;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 wi = work[w];
+    cache_sim(sims, wi.x, cache, cur, dep);
+    const SimDev& s = cache.s;
+    const Ctl& c = cache.c;
+    if (c.phase != PH_CHEB) continue;
+    const Geo g(s);
+    const int tile = wi.y * SPC + (int)threadIdx.x / SX;
+    const bool active = tile < s.w_ntiles;
+    const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
+    ChebPass<T> ps(s, c.cheb_k);
+    warp_tile_op<T, SX, NY>(
+        g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt, (T)s.theta,
+        true, [&](int m, bool live) { return ps.fetch(m, live); }, [&](const ChRaw<T>& v) { return ps.value(v); },
+        [&](int m, bool dir, T y, T v) { ps.out(m, dir, y, v); });
+    const T accv[1] = {ps.acc};
+    double tot[1];
+    if (finish_item<T, 1>(s, wi.y, s.w_items, accv, tot, red)) cheb_close(s, c, tot[0]);
   }
 }
 
@@ -919,8 +1103,13 @@ __global__ void __launch_bounds__(kPwThreads, pw_min_blocks(QPT, sizeof(T))) k_u
         sc->phase = PH_RESID;  // k_open recomputes r = b - A x and finishes the iteration
       } else {
         const double dn = pd[0];
-        sc->beta = dn / sc->delta;
-        sc->delta = dn;
+        // The stopping tests use r^T P^-1 r (Algorithm 1) with either
+        // preconditioner; with Chebyshev passes they form delta = r^T z and beta.
+        const bool ch = s.cheb_m >= 2;
+        if (!ch) {
+          sc->beta = dn / sc->delta;
+          sc->delta = dn;
+        }
         sc->iter += 1;
         sc->iter_step += 1;
         if (!isfinite(dn)) {
@@ -928,10 +1117,12 @@ __global__ void __launch_bounds__(kPwThreads, pw_min_blocks(QPT, sizeof(T))) k_u
         } else if (P == P_FP64) {
           if (dn <= sc->thresh) close_step(s, sc, dn);
           else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
+          else if (ch) enter_iter(s, sc);
         } else {
           const int cap = (P == P_FP32_PLAIN) ? s.max_iter : s.inner_max_iter;
           if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
           else if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
+          else if (ch) enter_iter(s, sc);
         }
       }
     }

@@ -71,7 +71,12 @@ def element_lam_max(p) -> float:
     the largest, over elements e, of sum_b |K^e_ab| / K^e_aa with
     K^e = rho_c_e M_e / dt + theta k_e K_e (the same for every corner a of a
     box element)."""
-    Me, Ke = fem.element_matrices(*fem.spacing(p.nx, p.ny, p.nz, p.extent))
+    h = fem.spacing(p.nx, p.ny, p.nz, p.extent)
+    if getattr(p, "element", "q1") == "p1":
+        from . import p1
+        Me, Ke = p1.box_matrices(*h)  # rows differ by corner: the maximum runs over them too
+    else:
+        Me, Ke = fem.element_matrices(*h)
     best = 0.0
     for rc, k in zip(np.asarray(p.rho_c, dtype=np.float64), np.asarray(p.k, dtype=np.float64)):
         E = rc / p.dt * Me + p.theta * k * Ke

@@ -1,6 +1,7 @@
 """Theta-scheme transient driver of the oracle (test infrastructure only).
 
-Each step solves the system of §3.1 divided by dt:
+Each step solves the system of §3.1 divided by dt (trilinear boxes, or the
+six-tetrahedra split of §4.1 when the problem's element is "p1"):
     A U^n = L U^{n-1} + F^n,  A = M/dt + theta K,  L = M/dt - (1-theta) K,
 with M, K assembled explicitly (the definition the assembly-free method must
 reproduce). Dirichlet nodes (a reading: the paper only has flux faces) are
@@ -14,7 +15,7 @@ from typing import List
 
 import numpy as np
 
-from . import fem, pcg as _pcg, precond as _precond
+from . import fem, p1 as _p1, pcg as _pcg, precond as _precond
 
 
 @dataclass
@@ -35,11 +36,12 @@ class System:
 
 
 def build_system(p) -> System:
-    M = fem.assemble(p.nx, p.ny, p.nz, p.extent, p.rho_c, "M")
-    K = fem.assemble(p.nx, p.ny, p.nz, p.extent, p.k, "K")
+    asm = _p1 if getattr(p, "element", "q1") == "p1" else fem
+    M = asm.assemble(p.nx, p.ny, p.nz, p.extent, p.rho_c, "M")
+    K = asm.assemble(p.nx, p.ny, p.nz, p.extent, p.k, "K")
     A = (M / p.dt + p.theta * K).tocsr()
     L = (M / p.dt - (1.0 - p.theta) * K).tocsr()
-    F = fem.flux_vector(p)
+    F = asm.flux_vector(p)
     dir_ids, dir_vals = fem.dirichlet_nodes(p)
     mask = np.ones(p.n_nodes, dtype=bool)
     mask[dir_ids] = False

@@ -46,6 +46,7 @@ class Problem:
     dt: float = 1e-3
     nsteps: int = 1
     rtol: float = 1e-10
+    element: str = "q1"  # "q1": trilinear boxes; "p1": six linear tetrahedra per box (§4.1)
 
     @property
     def n_nodes(self) -> int:

@@ -90,7 +90,22 @@ typedef struct {
   double cheb_ratio; /* Chebyshev interval [lam_hi / ratio, lam_hi] of
                         D^-1 A, lam_hi an element-wise Gershgorin bound
                         (see heat_cheb_interval), > 1                [10] */
+  int element;       /* heat_element: the finite element on each box of
+                        the mesh                                     [HEAT_ELEM_Q1] */
 } heat_params;
+
+/* Finite elements on the structured box mesh. Coefficients are per box in
+ * both cases (the same heat_set_coeffs layout). */
+typedef enum {
+  HEAT_ELEM_Q1 = 0, /* one trilinear hexahedron per box (§3.2's fixed grid) */
+  HEAT_ELEM_P1 = 1  /* six linear tetrahedra per box, all sharing the box
+                       diagonal from its lowest to its highest corner (the
+                       split of §4.1): for each ordering (a, b, c) of the
+                       axes, corners 0, e_a, e_a + e_b, 7. Face loads
+                       integrate the linear functions of the boundary
+                       triangles. Runs on block-tile kernels only (the
+                       tuning table's warp variants apply to Q1). */
+} heat_element;
 
 #define HEAT_CHEB_MAX_DEGREE 8
 

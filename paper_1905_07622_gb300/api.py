@@ -30,6 +30,9 @@ HEAT_FP64 = 0
 HEAT_FP32_REFINED = 1
 HEAT_FP32_PLAIN = 2
 PRECISIONS = {"fp64": HEAT_FP64, "fp32_refined": HEAT_FP32_REFINED, "fp32_plain": HEAT_FP32_PLAIN}
+HEAT_ELEM_Q1 = 0
+HEAT_ELEM_P1 = 1
+ELEMENTS = {"q1": HEAT_ELEM_Q1, "p1": HEAT_ELEM_P1}
 
 
 class HeatError(RuntimeError):
@@ -42,7 +45,8 @@ class heat_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("dt", C.c_double), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("resid_period", C.c_int), ("poll_period", C.c_int),
                 ("precision", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
-                ("inner_max_iter", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double)]
+                ("inner_max_iter", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
+                ("element", C.c_int)]
 
 
 class heat_bc(C.Structure):
@@ -223,6 +227,8 @@ def heat_params_default(**overrides) -> heat_params:
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "element" and isinstance(v, str):
+            v = ELEMENTS[v]
         setattr(p, k, v)
     return p
 
@@ -405,7 +411,7 @@ def make_request(p, precision="fp32_refined", **param_overrides):
     req.k = kk.ctypes.data
     req.u0 = u0.ctypes.data if u0 is not None else None
     req.bc = make_bc(p.dirichlet, p.flux, p.flux_steps)
-    kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision)
+    kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision, element=getattr(p, "element", "q1"))
     kw.update(param_overrides)
     req.params = heat_params_default(**kw)
     req.nsteps = int(p.nsteps)
@@ -676,7 +682,8 @@ class Simulation:
         mesh = heat_create_mesh(p.nx, p.ny, p.nz, p.origin, p.extent)
         try:
             nn, ne = heat_mesh_sizes(mesh)
-            kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision)
+            kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision=precision,
+                      element=getattr(p, "element", "q1"))
             kw.update(param_overrides)
             prm = heat_params_default(**kw)
             bc = make_bc(p.dirichlet, p.flux, p.flux_steps)

@@ -36,12 +36,12 @@ struct KernelSet {
   TileFn cheb, cheb_w;
 };
 
-template <int P, int SX, int SY>
+template <int P, int SX, int SY, int E = E_Q1>
 static KernelSet make_set() {
   using T = typename std::conditional<P == P_FP64, double, float>::type;
-  return {k_open<P, SX, SY>, k_apply_dot<T, SX, SY>, k_update<T, P, sizeof(T) == 4 ? 4 : 2>, SX, SY, SX * SY,
+  return {k_open<P, SX, SY, E>, k_apply_dot<T, SX, SY, E>, k_update<T, P, sizeof(T) == 4 ? 4 : 2>, SX, SY, SX * SY,
           SX * SY, nullptr, 0, 0, 0, pw_chunk(sizeof(T) == 4 ? 4 : 2), {512, 512, 512}, 0, false,
-          k_cheb<T, SX, SY>, nullptr};
+          k_cheb<T, SX, SY, E>, nullptr};
 }
 
 // Warp-segment apply variants the tuner chooses from: segment width, rows per
@@ -152,7 +152,17 @@ static TileFn update_kernel(int prec, int qpt) {
 // The kernels of precision prec under tuning table t. With Chebyshev passes
 // (cheb) a fused variant is replaced by the register-prefetch variant of the
 // same segment shape: the fused iteration has no place for the passes.
-static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false) {
+static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int elem = E_Q1) {
+  if (elem == E_P1) {  // block tiles only: the warp variants are trilinear
+    KernelSet k = prec == P_FP64 ? make_set<P_FP64, 16, 16, E_P1>()
+                                 : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16, E_P1>()
+                                                            : make_set<P_FP32_PLAIN, 16, 16, E_P1>());
+    for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
+    const int qpt = t.pw_quads[prec];
+    k.pw_chunk = pw_chunk(qpt);
+    k.update = update_kernel(prec, qpt);
+    return k;
+  }
   int variant = t.variant[prec];
   if (cheb && variant >= 0 && variant < kNumVariants && kVariants[variant].fused) {
     const WVariant& f = kVariants[variant];
@@ -223,6 +233,7 @@ struct Engine {
   double* d_partial = nullptr;
   long long cap_op = 0, cap_pw = 0, cap_partial = 0;
   int grid_op = 0, grid_pw = 0, iters_per_tick = 4;
+  int elem = E_Q1;  // the members' finite element (one per engine)
   int ncheb = 0;    // Chebyshev passes per iteration in the tick: max over members of degree - 1
   int grid_ch = 0;  // grid of the pass kernel
   cudaGraph_t graph = nullptr;
@@ -426,8 +437,14 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   Engine* e = new Engine();
   e->sims.assign(sims, sims + nsims);
   e->prec = precision;
+  e->elem = sims[0]->dev.elem;
+  for (int i = 1; i < nsims; ++i)
+    if (sims[i]->dev.elem != e->elem) {
+      delete e;
+      return set_error(HEAT_ERR_ARG, "engine: the simulations of one batch must share the element type");
+    }
   e->ncheb = members_ncheb(e);
-  e->ks = kernel_set(precision, tun ? *tun : tuning_get(), e->ncheb > 0);
+  e->ks = kernel_set(precision, tun ? *tun : tuning_get(), e->ncheb > 0, e->elem);
   e->stream = stream;
   // capacities: the geometry is a function of each mesh, so compute it
   long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_partial = 0;
@@ -503,8 +520,10 @@ heat_status engine_refresh(Engine* e) {
   // with them the kernel set (no fused iteration with passes) and the graph
   const int nch = members_ncheb(e);
   const bool recapture = nch != e->ncheb;
+  for (const heat_sim* s : e->sims)
+    if (s->dev.elem != e->elem) return set_error(HEAT_ERR_ARG, "engine: a member changed its element type");
   if ((nch > 0) != (e->ncheb > 0)) {
-    const KernelSet ks = kernel_set(e->prec, tuning_get(), nch > 0);
+    const KernelSet ks = kernel_set(e->prec, tuning_get(), nch > 0, e->elem);
     bool same_shape = ks.wsx == e->ks.wsx && ks.wny == e->ks.wny && ks.wwarps == e->ks.wwarps &&
                       ks.pw_chunk == e->ks.pw_chunk && (ks.apply_w != nullptr) == (e->ks.apply_w != nullptr);
     for (int b = 0; b < 3; ++b) same_shape = same_shape && ks.seg_nodes[b] == e->ks.seg_nodes[b];
@@ -806,8 +825,12 @@ heat_status prime_products(heat_sim* s, int nslots) {
   const int ntz = (d.nz + 1 + TZ - 1) / TZ;
   const long long grid = (long long)ntx * nty * ntz;
   if (grid > (1LL << 31) - 1) return set_error(HEAT_ERR_ARG, "prime_products: mesh too large");
-  for (int v = 0; v < nslots; ++v)
-    k_product<SX, SY><<<(unsigned)grid, SX * SY, 0, s->stream>>>(s->d_dev, d.vec64[v], d.yv[v], ntx, nty, TZ);
+  for (int v = 0; v < nslots; ++v) {
+    if (d.elem == E_P1)
+      k_product<SX, SY, E_P1><<<(unsigned)grid, SX * SY, 0, s->stream>>>(s->d_dev, d.vec64[v], d.yv[v], ntx, nty, TZ);
+    else
+      k_product<SX, SY><<<(unsigned)grid, SX * SY, 0, s->stream>>>(s->d_dev, d.vec64[v], d.yv[v], ntx, nty, TZ);
+  }
   CUDA_TRY(cudaGetLastError());
   return HEAT_OK;
 }

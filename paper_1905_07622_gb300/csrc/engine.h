@@ -43,6 +43,9 @@ heat_status set_error(heat_status st, const char* fmt, ...);
 void element_classes(double hx, double hy, double hz, double mhat[8], double khat[8]);
 // The same element matrices' eigenvalues in the corners' Walsh basis, / 8.
 void walsh_eigenvalues(double hx, double hy, double hz, double lam_m[8], double lam_k[8]);
+// 8x8 mass (M, row-major by local corner) and stiffness (K) of an hx*hy*hz
+// box split into six linear tetrahedra (heat.h HEAT_ELEM_P1).
+void p1_box_matrices(double hx, double hy, double hz, double M[64], double K[64]);
 heat_status sim_alloc(heat_sim* s, void** p, size_t bytes);
 heat_status sim_upload_desc(heat_sim* s);
 heat_status sim_read_scalars(heat_sim* s);

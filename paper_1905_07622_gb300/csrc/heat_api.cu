@@ -61,6 +61,7 @@ extern "C" void heat_params_default(heat_params* p) {
   p->inner_max_iter = 2000;
   p->cheb_degree = 0;
   p->cheb_ratio = 10.0;
+  p->element = HEAT_ELEM_Q1;
 }
 
 extern "C" heat_status heat_create_mesh(int nx, int ny, int nz, const double origin[3],
@@ -135,6 +136,35 @@ void heat::walsh_eigenvalues(double hx, double hy, double hz, double lam_m[8], d
   }
 }
 
+// The six tetrahedra of a box are the monotone corner paths 0 -> e_a ->
+// e_a + e_b -> 7 over the orderings (a, b, c) of the axes, each of volume
+// V = hx hy hz / 6. On such a tetrahedron the linear interpolant is
+//   u = u_0 + (u_1 - u_0) x_a / h_a + (u_2 - u_1) x_b / h_b + (u_3 - u_2) x_c / h_c,
+// so the gradients of the four vertex functions are -e_a/h_a,
+// e_a/h_a - e_b/h_b, e_b/h_b - e_c/h_c and e_c/h_c; the element matrices are
+// K_ij = V g_i . g_j and the P1 mass V (1 + delta_ij) / 20.
+void heat::p1_box_matrices(double hx, double hy, double hz, double M[64], double K[64]) {
+  const double h[3] = {hx, hy, hz};
+  const double vol = hx * hy * hz / 6.0;
+  for (int t = 0; t < 64; ++t) M[t] = K[t] = 0.0;
+  const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (const auto& o : orders) {
+    const int v[4] = {0, 1 << o[0], (1 << o[0]) | (1 << o[1]), 7};
+    double g[4][3] = {};
+    g[0][o[0]] = -1.0 / h[o[0]];
+    g[1][o[0]] = 1.0 / h[o[0]];
+    g[1][o[1]] = -1.0 / h[o[1]];
+    g[2][o[1]] = 1.0 / h[o[1]];
+    g[2][o[2]] = -1.0 / h[o[2]];
+    g[3][o[2]] = 1.0 / h[o[2]];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        M[8 * v[a] + v[b]] += vol * (a == b ? 2.0 : 1.0) / 20.0;
+        K[8 * v[a] + v[b]] += vol * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+      }
+  }
+}
+
 // ------------------------------------------------------------------ sim
 
 static int grid_for(long long n, int block) {
@@ -174,6 +204,8 @@ static heat_status check_params(const heat_params* p) {
   }
   if (p->cheb_degree < 0 || p->cheb_degree > HEAT_CHEB_MAX_DEGREE)
     return set_error(HEAT_ERR_ARG, "cheb_degree must be in [0, %d] (got %d)", HEAT_CHEB_MAX_DEGREE, p->cheb_degree);
+  if (p->element != HEAT_ELEM_Q1 && p->element != HEAT_ELEM_P1)
+    return set_error(HEAT_ERR_ARG, "element must be HEAT_ELEM_Q1 or HEAT_ELEM_P1 (got %d)", p->element);
   if (p->cheb_degree >= 2 && !(p->cheb_ratio > 1.0 && std::isfinite(p->cheb_ratio)))
     return set_error(HEAT_ERR_ARG, "cheb_ratio must be finite and > 1 (got %g)", p->cheb_ratio);
   return HEAT_OK;
@@ -191,6 +223,7 @@ static void fill_params(heat_sim* s) {
   d.inner_max_iter = s->prm.inner_max_iter;
   d.cheb_m = s->prm.cheb_degree >= 2 ? s->prm.cheb_degree : 0;  // degree 1 is Jacobi scaled by a constant
   d.prec = s->prm.precision;
+  d.elem = s->prm.element;
 }
 
 heat_status heat::sim_upload_desc(heat_sim* s) {
@@ -357,6 +390,8 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   ALLOC(s->d_sc, sizeof(SimScalars), SimScalars*);
   ALLOC(s->d_q6, sizeof(double) * 6, double*);
   ALLOC(s->d_bad, sizeof(unsigned int), unsigned int*);
+  ALLOC(d.p1w, sizeof(double) * 128, const double*);
+  ALLOC(d.p1w_f, sizeof(float) * 128, const float*);
 #undef ALLOC
   d.sc = s->d_sc;
   if (cudaMallocHost((void**)&s->h_sc, sizeof(SimScalars)) != cudaSuccess) {
@@ -369,6 +404,10 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   {
     // default state: rho_c = k = 1, U^0 = 0 (Dirichlet nodes at their values)
     std::vector<double2> ones((size_t)s->ne, make_double2(1.0, 1.0));
+    double p1w[128];
+    float p1w_f[128];
+    p1_box_matrices(hx, hy, hz, p1w, p1w + 64);
+    for (int t = 0; t < 128; ++t) p1w_f[t] = (float)p1w[t];
     if (cudaMemcpy((void*)d.coef, ones.data(), (size_t)s->ne * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemsetAsync(d.vec64[0], 0, N8, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.vec64[1], 0, N8, s->stream) != cudaSuccess ||
@@ -383,6 +422,8 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
         cudaMemsetAsync(d.wc32[1], 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.z32, 0, N4, s->stream) != cudaSuccess ||
         cudaMemsetAsync(d.cheb, 0, sizeof(double) * 20, s->stream) != cudaSuccess ||
+        cudaMemcpy((void*)d.p1w, p1w, sizeof(p1w), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy((void*)d.p1w_f, p1w_f, sizeof(p1w_f), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpyAsync(s->d_q6, b.flux, sizeof(double) * 6, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
       st = set_error(HEAT_ERR_CUDA, "heat_sim_create: initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
       goto fail;
@@ -466,12 +507,19 @@ extern "C" heat_status heat_set_params(heat_sim* s, const heat_params* params) {
   if (!s) return set_error(HEAT_ERR_ARG, "heat_set_params: sim is NULL");
   heat_status st = check_params(params);
   if (st != HEAT_OK) return st;
-  const bool prec_changed = params->precision != s->prm.precision;
+  const bool elem_changed = params->element != s->prm.element;
+  const bool prec_changed = params->precision != s->prm.precision || elem_changed;
   s->prm = *params;
   fill_params(s);
   if (prec_changed) {
     engine_destroy(s->eng);
     s->eng = nullptr;
+  }
+  if (elem_changed) {  // the face loads depend on the element
+    st = sim_upload_desc(s);
+    if (st != HEAT_OK) return st;
+    st = sim_setup_flux(s);
+    if (st != HEAT_OK) return st;
   }
   st = sim_refresh(s);
   if (st != HEAT_OK) return st;

@@ -23,6 +23,19 @@ enum Phase : int {
 
 enum Prec : int { P_FP64 = 0, P_FP32_REFINED = 1, P_FP32_PLAIN = 2 };
 
+// Finite element on each box (heat.h heat_element).
+enum Elem : int { E_Q1 = 0, E_P1 = 1 };
+
+// Local corners c, d of a box (c = x | y<<1 | z<<2) share a tetrahedron of
+// the six-tetrahedra split iff one is a bitwise subset of the other (the
+// tetrahedra are the monotone paths 0 -> e_a -> e_a+e_b -> 7); their
+// stiffness coupling vanishes unless they differ in one coordinate at most
+// (the gradients of the path's linear functions are axis-aligned).
+__host__ __device__ constexpr bool p1_mass_nz(int c, int d) { return (c & d) == c || (c & d) == d; }
+__host__ __device__ constexpr bool p1_stiff_nz(int c, int d) {
+  return c == d || (c ^ d) == 1 || (c ^ d) == 2 || (c ^ d) == 4;
+}
+
 // Status codes shared with heat.h.
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_NONFINITE = 5, ST_BREAKDOWN = 8 };
 
@@ -76,6 +89,8 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   int max_iter, resid_period, max_outer, flux_steps;
   int inner_max_iter;
   int cheb_m;                 // Chebyshev preconditioner degree (>= 2), 0: Jacobi (Algorithm 1)
+  int elem;                   // Elem: finite element on each box
+  int pad_elem_;
   double g[6];                // Dirichlet values
   double inv_dt, theta, rtol, inner_rtol;
   double mhat[8], khat[8];    // element mass/stiffness entry by corner XOR pattern
@@ -118,6 +133,11 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   // 2 rho_k / delta (k = 1..7), [16] lam_lo, [17] lam_hi, [18] the bound's
   // running maximum as bits (see k_cheb_bound)
   double* cheb;
+  // Six-tetrahedra boxes (elem == E_P1): the box's 8x8 mass and stiffness
+  // matrices M' (entries 0..63, row-major by local corner) and K' (64..127),
+  // FP64 and FP32 copies.
+  const double* p1w;
+  const float* p1w_f;
   double* partial;            // 2 per tile
   int* iters_log;             // CG iterations of each step
   int iters_log_len;

@@ -123,13 +123,18 @@ static void worker_loop(heat_server* srv) {
         srv->cv_work.wait_for(lock, std::chrono::milliseconds(50));
         continue;
       }
-      // one engine runs one precision: a request of another precision waits
-      // until the running set has drained
+      // one engine runs one precision and one element type: a request of
+      // another waits until the running set has drained
       int prec = srv->active.empty() ? -1 : srv->active[0]->r.params.precision;
+      int elem = srv->active.empty() ? -1 : srv->active[0]->r.params.element;
       for (auto it = srv->pending.begin(); it != srv->pending.end();) {
         Req* q = *it;
-        if (prec < 0) prec = q->r.params.precision;
-        if (q->r.params.precision == prec && (int)(srv->active.size() + admit.size()) < srv->max_active &&
+        if (prec < 0) {
+          prec = q->r.params.precision;
+          elem = q->r.params.element;
+        }
+        if (q->r.params.precision == prec && q->r.params.element == elem &&
+            (int)(srv->active.size() + admit.size()) < srv->max_active &&
             srv->used + q->footprint <= srv->budget) {
           srv->used += q->footprint;
           q->state = RQ_ACTIVE;

@@ -10,7 +10,8 @@ namespace heat {
 // --------------------------------------------------- per-node (setup) kernels
 
 // Jacobi diagonal (§3.3): P_i = sum_{e contains i} (rho_c_e/dt * Mhat[0] + theta*k_e*Khat[0]),
-// P = 1 on Dirichlet rows. Writes 1/P in FP64 and FP32.
+// P = 1 on Dirichlet rows (six-tetrahedra boxes: the diagonal entry M'_cc,
+// K'_cc of the node's local corner c in each box). Writes 1/P in FP64 and FP32.
 __global__ void k_setup_diag(const SimDev* __restrict__ sp) {
   const SimDev& s = *sp;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < s.nn;
@@ -24,10 +25,15 @@ __global__ void k_setup_diag(const SimDev* __restrict__ sp) {
         const int ex = i - (c & 1), ey = j - ((c >> 1) & 1), ez = k - ((c >> 2) & 1);
         if (ex < 0 || ey < 0 || ez < 0 || ex >= s.nx || ey >= s.ny || ez >= s.nz) continue;
         const double2 cf = s.coef[ex + (long long)s.nx * (ey + (long long)s.ny * ez)];
-        sa += cf.x;
-        sk += cf.y;
+        if (s.elem == E_P1) {
+          sa += cf.x * s.p1w[9 * c];
+          sk += cf.y * s.p1w[64 + 9 * c];
+        } else {
+          sa += cf.x;
+          sk += cf.y;
+        }
       }
-      p = s.inv_dt * s.mhat[0] * sa + s.theta * s.khat[0] * sk;
+      p = s.elem == E_P1 ? s.inv_dt * sa + s.theta * sk : s.inv_dt * s.mhat[0] * sa + s.theta * s.khat[0] * sk;
     }
     s.pinv[n] = 1.0 / p;
     s.pinv32[n] = (float)(1.0 / p);
@@ -51,6 +57,14 @@ __global__ void k_cheb_bound(const SimDev* __restrict__ sp) {
        e += (long long)gridDim.x * blockDim.x) {
     const double2 cf = s.coef[e];
     const double a = s.inv_dt * cf.x, b = s.theta * cf.y;
+    if (s.elem == E_P1) {  // the rows differ by corner: the maximum runs over them
+      for (int c = 0; c < 8; ++c) {
+        double row = 0.0;
+        for (int d = 0; d < 8; ++d) row += fabs(a * s.p1w[8 * c + d] + b * s.p1w[64 + 8 * c + d]);
+        best = fmax(best, row / (a * s.p1w[9 * c] + b * s.p1w[64 + 9 * c]));
+      }
+      continue;
+    }
     double row = 0.0;
     for (int p = 0; p < 8; ++p) row += fabs(a * s.mhat[p] + b * s.khat[p]);
     best = fmax(best, row / (a * s.mhat[0] + b * s.khat[0]));
@@ -98,9 +112,24 @@ __device__ __forceinline__ double face_sum(const double* q, int na, int nb, int 
   return f;
 }
 
+// The six-tetrahedra split cuts each boundary quad along its diagonal from
+// the lower to the upper corner (in the face's own coordinates a < b), into
+// two triangles of area A/2, each giving its vertices q A/6: a node receives
+// q A/3 from the quads whose diagonal it ends (lower-left, upper-right) and
+// q A/6 from the two others. Returns the sum of q times those shares / A.
+__device__ __forceinline__ double face_sum_p1(const double* q, double qu, int na, int nb, int a, int b) {
+  double f = 0.0;
+  for (int db = -1; db <= 0; ++db)
+    for (int da = -1; da <= 0; ++da) {
+      const int ea = a + da, eb = b + db;
+      if (ea >= 0 && ea < na && eb >= 0 && eb < nb) f += (q ? q[ea + na * eb] : qu) * (da == db ? 1.0 / 3.0 : 1.0 / 6.0);
+    }
+  return f;
+}
+
 // Face flux vector F_i = int_face q phi_i ds: on a face of h_a*h_b quads each
 // node gets q*h_a*h_b/4 per adjacent quad (1, 2 or 4 of them), with q the
-// face's uniform value or the quad's own.
+// face's uniform value or the quad's own (six-tetrahedra boxes: face_sum_p1).
 __global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __restrict__ q6, FaceFlux ff,
                              double hx, double hy, double hz) {
   const SimDev& s = *sp;
@@ -111,6 +140,17 @@ __global__ void k_setup_flux(const SimDev* __restrict__ sp, const double* __rest
     const int ni = (i > 0 && i < s.nx) ? 2 : 1;
     const int nj = (j > 0 && j < s.ny) ? 2 : 1;
     const int nk = (k > 0 && k < s.nz) ? 2 : 1;
+    if (s.elem == E_P1) {
+      double f = 0.0;
+      if (i == 0) f += face_sum_p1(ff.q[0], q6[0], s.ny, s.nz, j, k) * hy * hz;
+      if (i == s.nx) f += face_sum_p1(ff.q[1], q6[1], s.ny, s.nz, j, k) * hy * hz;
+      if (j == 0) f += face_sum_p1(ff.q[2], q6[2], s.nx, s.nz, i, k) * hx * hz;
+      if (j == s.ny) f += face_sum_p1(ff.q[3], q6[3], s.nx, s.nz, i, k) * hx * hz;
+      if (k == 0) f += face_sum_p1(ff.q[4], q6[4], s.nx, s.ny, i, j) * hx * hy;
+      if (k == s.nz) f += face_sum_p1(ff.q[5], q6[5], s.nx, s.ny, i, j) * hx * hy;
+      s.F[n] = is_dirichlet(s, i, j, k) ? 0.0 : f;
+      continue;
+    }
     const double ax = hy * hz * 0.25, ay = hx * hz * 0.25, az = hx * hy * 0.25;
     double f = 0.0;
     if (i == 0) f += ff.q[0] ? face_sum(ff.q[0], s.ny, s.nz, j, k) * ax : q6[0] * ax * nj * nk;

@@ -12,10 +12,40 @@ namespace heat {
 
 // ------------------------------------------------------------ the operator
 
+template <class T> __device__ __forceinline__ const T* p1_weights(const SimDev& s);
+template <> __device__ __forceinline__ const double* p1_weights<double>(const SimDev& s) { return s.p1w; }
+template <> __device__ __forceinline__ const float* p1_weights<float>(const SimDev& s) { return s.p1w_f; }
+
+// The six-tetrahedra form of gather_apply: node (i,j,k) is local corner c of
+// each of its <= 8 boxes, and row c of the box matrices M', K' couples it to
+// the corners d of the tetrahedra it shares (p1_mass_nz, p1_stiff_nz).
+template <class T, class Load>
+__device__ __forceinline__ T gather_apply_p1(const SimDev& s, T sa, T sb, int i, int j, int k, Load&& ld) {
+  const auto* coef = coef_ptr<T>(s);
+  const T* w = p1_weights<T>(s);
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ex = i - (c & 1), ey = j - ((c >> 1) & 1), ez = k - ((c >> 2) & 1);
+    if (ex < 0 || ey < 0 || ez < 0 || ex >= s.nx || ey >= s.ny || ez >= s.nz) continue;
+    const auto cf = coef[ex + (long long)s.nx * (ey + (long long)s.ny * ez)];
+    const T wa = sa * cf.x, wb = sb * cf.y;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      if (!p1_mass_nz(c, d)) continue;
+      const T m = w[8 * c + d], kk = p1_stiff_nz(c, d) ? w[64 + 8 * c + d] : T(0);
+      acc += (wa * m + wb * kk) * ld(ex + (d & 1), ey + ((d >> 1) & 1), ez + ((d >> 2) & 1));
+    }
+  }
+  return acc;
+}
+
 // y at node (i,j,k) of sum_e (sa*rho_c_e*Mhat + sb*k_e*Khat) x_e, with x
 // supplied by a loader ld(ii,jj,kk) for the 27 neighbours (0 outside the mesh).
+// Six-tetrahedra boxes take gather_apply_p1.
 template <class T, class Load>
 __device__ __forceinline__ T gather_apply(const SimDev& s, T sa, T sb, int i, int j, int k, Load&& ld) {
+  if (s.elem == E_P1) return gather_apply_p1<T>(s, sa, sb, i, j, k, ld);
   T v[27];
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)

@@ -24,6 +24,7 @@
 #pragma once
 
 #include "op.cuh"
+#include "op_p1.cuh"
 #include "op_warp.cuh"
 
 namespace heat {
@@ -248,10 +249,10 @@ struct D2 {
   double a, b;
 };
 
-template <int P, int SX, int SY>
+template <int P, int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                  const int* __restrict__ nwork_p) {
-  __shared__ TileSmem<double, SX, SY> sh;
+  __shared__ OpSmem<E, double, SX, SY> sh;
   __shared__ double red[3 * 32];
   __shared__ ItemCache cache;
   int cur = -1;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       const double* __restrict__ y1 = s.yv[c.iu1];
       const double* __restrict__ y2 = s.yv[c.iu2];
       // pass 1: b = L u^{n-1} + F^n - A_{.D} g (free rows), g (Dirichlet rows)
-      tile_op<double, SX, SY>(
+      tile_op_e<E, double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta - 1.0, false, sh,
           [&](int m, bool live) -> double { return live ? u1[m] : 0.0; }, ident,
           [&](int m, bool dir, double y, double v) {
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
             }
           });
       // pass 2: x0 = 2u^{n-1} - u^{n-2} (u^{n-1} on the first step), r = b - A' x0
-      if (!use_y) tile_op<double, SX, SY>(
+      if (!use_y) tile_op_e<E, double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> D2 {
             if (!live) return {0.0, 0.0};
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       double* __restrict__ xa = s.vec64[c.ixa];
       double* __restrict__ ya = s.yv[c.ixa];  // A' x64, used by the next step if this one closes
       const float* __restrict__ e32 = s.e32;
-      tile_op<double, SX, SY>(
+      tile_op_e<E, double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> D2 {
             if (!live) return {0.0, 0.0};
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
     } else {  // PH_RESID (FP64): r = b - A' x, x already advanced by k_update
       const double* __restrict__ x = s.vec64[c.ix];
       double* __restrict__ r = s.r;
-      tile_op<double, SX, SY>(
+      tile_op_e<E, double, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> double { return live ? x[m] : 0.0; }, ident,
           [&](int m, bool dir, double y, double) {
@@ -452,17 +453,17 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
 // where its tile starts. One block per tile of (SX-1) x (SY-1) node columns
 // and tz levels. Restores the stored products A' U^{n-1}, A' U^{n-2} of a
 // resumed simulation (see k_open, phase OPEN).
-template <int SX, int SY>
+template <int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_product(const SimDev* __restrict__ sd, const double* __restrict__ u,
                                                      double* __restrict__ y, int ntx, int nty, int tz) {
-  __shared__ TileSmem<double, SX, SY> sh;
+  __shared__ OpSmem<E, double, SX, SY> sh;
   const SimDev& s = *sd;
   const Geo g(s);
   const int t = blockIdx.x;
   const int tx = t % ntx, rem = t / ntx, ty = rem % nty, tk = rem / nty;
   const int k0 = tk * tz;
   const int nzt = min(tz, s.nz + 1 - k0);
-  tile_op<double, SX, SY>(
+  tile_op_e<E, double, SX, SY>(
       g, s, s.coef, tx * (SX - 1), ty * (SY - 1), k0, nzt, s.inv_dt, s.theta, true, sh,
       [&](int m, bool live) -> double { return live ? u[m] : 0.0; }, [](double v) { return v; },
       [&](int m, bool dir, double yv, double) {
@@ -505,10 +506,10 @@ struct DirRaw {
   T p, r, d;
 };
 
-template <class T, int SX, int SY>
+template <class T, int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                       const int* __restrict__ nwork_p) {
-  __shared__ TileSmem<T, SX, SY> sh;
+  __shared__ OpSmem<E, T, SX, SY> sh;
   __shared__ double red[32];
   __shared__ ItemCache cache;
   int cur = -1;
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
     const T beta = rs ? T(0) : (T)c.beta;
     // Per-thread partial in T (FP32 on the FP32 path), FP64 from the warp sums on.
     T acc = T(0);
-    tile_op<T, SX, SY>(
+    tile_op_e<E, T, SX, SY>(
         g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
         [&](int m, bool live) -> DirRaw<T> {
           if (!live) return {T(0), T(0), T(0)};
@@ -732,10 +733,10 @@ __device__ __forceinline__ void cheb_close(const SimDev& s, const Ctl& c, double
   }
 }
 
-template <class T, int SX, int SY>
+template <class T, int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_cheb(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                  const int* __restrict__ nwork_p) {
-  __shared__ TileSmem<T, SX, SY> sh;
+  __shared__ OpSmem<E, T, SX, SY> sh;
   __shared__ double red[32];
   __shared__ ItemCache cache;
   int cur = -1;
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(SX* SY) k_cheb(const SimDev* __restrict__ sims
     const Geo g(s);
     const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
     ChebPass<T> ps(s, c.cheb_k);
-    tile_op<T, SX, SY>(
+    tile_op_e<E, T, SX, SY>(
         g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
         [&](int m, bool live) { return ps.fetch(m, live); }, [&](const ChRaw<T>& v) { return ps.value(v); },
         [&](int m, bool dir, T y, T v) { ps.out(m, dir, y, v); });

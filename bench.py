@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--cheb-degrees", default="2,3",
                     help="Chebyshev-Jacobi degrees timed on the layered FP32-refined leg ('' to skip)")
     ap.add_argument("--cheb-ratio", type=float, default=10.0, help="Chebyshev interval ratio lam_hi / lam_lo")
+    ap.add_argument("--p1-steps", type=int, default=30,
+                    help="six-tetrahedra leg: steps of the inclusions workload on P1 and Q1 elements (0: skip)")
+    ap.add_argument("--p1-only", action="store_true", help="run only the six-tetrahedra leg")
     ap.add_argument("--mh-chains", type=int, default=32,
                     help="corrosion inverse problem: Metropolis-Hastings chains solved as one batch (0: skip)")
     ap.add_argument("--mh-iters", type=int, default=8)
@@ -438,6 +441,43 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
     return out
 
 
+def run_p1(hg, torch, nsteps: int, stream):
+    """The inclusions workload on six-tetrahedra boxes (§4.1's element: 6
+    million linear tetrahedra on the 100^3 grid, 1,030,301 DOF), FP32-refined,
+    first `nsteps` of its 300 steps; plus the P1 apply kernel timed alone after
+    an L2 flush. The trilinear leg's numbers for the same steps are the
+    comparison."""
+    import workloads as W
+    out = {"workload": f"inclusions_cube_100 on six-tetrahedra boxes (6,000,000 tetrahedra, 1,030,301 DOF), "
+                       f"first {nsteps} of its 300 steps, FP32-refined, rtol 1e-10"}
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peak, _ = measured_peaks()
+    for element in ("p1", "q1"):
+        p = W.inclusions_cube(nsteps=nsteps)
+        p.element = element
+        with hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream) as s:
+            s.step(1)  # warm-up (graph capture)
+            hg.heat_set_state(s.sim, p.u0, s.n_nodes)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = s.step(nsteps)
+            e.record(stream)
+            e.synchronize()
+            sec = a.elapsed_time(e) / 1e3
+            torch.cuda.nvtx.range_push(f"roofline_{element}")
+            prof = hg.heat_profile_iteration(s.sim, 40, flush)
+            torch.cuda.nvtx.range_pop()
+        achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
+        out[element] = {"ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"], "status": st["status"],
+                        "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec,
+                        "apply": {"ms_per_launch": prof["ms_apply"], "achieved_gbs": achieved, "peak_gbs": peak,
+                                  "frac": achieved / peak, "algorithmic_bytes_per_launch": prof["bytes_apply"]},
+                        "update_ms_per_launch": prof["ms_update"]}
+    return out
+
+
 def run_mh(hg, torch, nchains: int, niter: int, stream):
     """The §5.3 inverse problem on a synthetic plate (corrosion_plate: 64 x 20 x 64
     elements, 88,725 DOF, 100 steps of 0.1 s): camera data from the GPU forward
@@ -551,6 +591,9 @@ def main():
                                                  not (args.no_autotune or args.tuning_json),
                                                  cheb_degrees(args), args.cheb_ratio)}), flush=True)
         return
+    if args.p1_only:  # the six-tetrahedra leg alone (used for profiling captures)
+        print(json.dumps({"tetrahedra": run_p1(hg, torch, args.p1_steps, stream)}), flush=True)
+        return
     if args.batch_only:  # the batched workload alone (used for profiling captures)
         fixed = bool(args.tuning_json)
         if fixed:
@@ -651,7 +694,7 @@ def main():
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
     traffic = ncu_traffic(kernel_key)
 
-    batched = serving = layered = mh = None
+    batched = serving = layered = mh = p1 = None
     if rank == 0 and args.batch_sims > 0:
         batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
     if rank == 0 and args.layered_steps > 0:
@@ -659,6 +702,8 @@ def main():
                               cheb_degrees(args), args.cheb_ratio)
     if rank == 0 and args.mh_chains > 0:
         mh = run_mh(hg, torch, args.mh_chains, args.mh_iters, stream)
+    if rank == 0 and args.p1_steps > 0:
+        p1 = run_p1(hg, torch, args.p1_steps, stream)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 
@@ -689,6 +734,7 @@ def main():
             "batched": batched,
             "layered": layered,
             "inverse_problem": mh,
+            "tetrahedra": p1,
             "serving": serving,
         }
         if cpu is not None:

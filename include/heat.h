@@ -103,8 +103,8 @@ typedef enum {
                        split of §4.1): for each ordering (a, b, c) of the
                        axes, corners 0, e_a, e_a + e_b, 7. Face loads
                        integrate the linear functions of the boundary
-                       triangles. Runs on block-tile kernels only (the
-                       tuning table's warp variants apply to Q1). */
+                       triangles. Every kernel variant of the tuning
+                       table has a P1 form. */
 } heat_element;
 
 #define HEAT_CHEB_MAX_DEGREE 8

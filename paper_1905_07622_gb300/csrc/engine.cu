@@ -46,42 +46,53 @@ static KernelSet make_set() {
 
 // Warp-segment apply variants the tuner chooses from: segment width, rows per
 // lane, warps per block, cp.async stages (0: register prefetch); f64 is null
-// where the FP64 registers or shared memory do not fit.
+// where the FP64 registers or shared memory do not fit. Each kernel exists
+// for both elements (the march differs, op_warp.cuh); index 0 trilinear
+// boxes, 1 six-tetrahedra boxes.
 struct WVariant {
   int sx, ny, warps, stages;
-  TileFn f32, f64;
+  TileFn f32[2], f64[2];
   int smem32, smem64;  // dynamic shared memory per block
   bool fused;          // FP32 only: the fused iteration kernel k_cg_iter
-  TileFn cheb32, cheb64;  // Chebyshev passes of this segment shape (null: fused)
+  TileFn cheb32[2], cheb64[2];  // Chebyshev passes of this segment shape (null: fused)
 };
 // One register-prefetch Chebyshev pass kernel per segment shape and type,
 // bounded like that shape's register-prefetch apply (FP64: one block per SM).
-template <class T, int SX, int NY, int W, bool ON>
+template <class T, int SX, int NY, int W, bool ON, int E>
 static constexpr TileFn chebfn() {
   if constexpr (!ON) {
     return nullptr;
   } else if constexpr (sizeof(T) == 8) {
-    return k_cheb_w<double, SX, NY, W, 1>;
+    return k_cheb_w<double, SX, NY, W, 1, E>;
   } else {
     constexpr int MINB = (SX == 16 && NY == 2) ? 2 : ((SX == 32 && NY == 2) ? 4 : 3);
-    return k_cheb_w<float, SX, NY, W, MINB>;
+    return k_cheb_w<float, SX, NY, W, MINB, E>;
   }
 }
-template <class T, int SX, int NY, int W, int S, int MINB, bool ON>
+template <class T, int SX, int NY, int W, int S, int MINB, bool ON, int E>
 static constexpr TileFn wfn() {
-  if constexpr (ON) return k_apply_dot_w<T, SX, NY, W, S, MINB>;
+  if constexpr (ON) return k_apply_dot_w<T, SX, NY, W, S, MINB, E>;
   else return nullptr;
 }
 template <int SX, int NY, int W, int S, int MINB, int MINB64>
 static constexpr WVariant wv() {
-  return {SX, NY, W, S, wfn<float, SX, NY, W, S, MINB, true>(), wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0)>(),
+  return {SX,
+          NY,
+          W,
+          S,
+          {wfn<float, SX, NY, W, S, MINB, true, E_Q1>(), wfn<float, SX, NY, W, S, MINB, true, E_P1>()},
+          {wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0), E_Q1>(),
+           wfn<double, SX, NY, W, S, MINB64, (MINB64 > 0), E_P1>()},
           S ? 32 * W * async_stage_bytes<float, NY, (S ? S : 2)>() : 0,
-          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0, false, chebfn<float, SX, NY, W, true>(),
-          chebfn<double, SX, NY, W, (MINB64 > 0)>()};
+          S ? 32 * W * async_stage_bytes<double, NY, (S ? S : 2)>() : 0,
+          false,
+          {chebfn<float, SX, NY, W, true, E_Q1>(), chebfn<float, SX, NY, W, true, E_P1>()},
+          {chebfn<double, SX, NY, W, (MINB64 > 0), E_Q1>(), chebfn<double, SX, NY, W, (MINB64 > 0), E_P1>()}};
 }
 template <int SX, int NY, int W, int MINB>
 static constexpr WVariant wv_fused() {
-  return {SX, NY, W, 0, k_cg_iter<SX, NY, W, MINB>, nullptr, 0, 0, true, nullptr, nullptr};
+  return {SX, NY, W, 0, {k_cg_iter<SX, NY, W, MINB, E_Q1>, k_cg_iter<SX, NY, W, MINB, E_P1>}, {nullptr, nullptr},
+          0,  0,  true, {nullptr, nullptr}, {nullptr, nullptr}};
 }
 // (segment width, rows, warps, stages, min blocks per SM for float / double,
 // 0 = no double kernel)
@@ -107,7 +118,7 @@ bool variant_info(int v, int info[6]) {
   info[0] = kVariants[v].sx;
   info[1] = kVariants[v].ny;
   info[2] = kVariants[v].warps;
-  info[3] = kVariants[v].f64 != nullptr;
+  info[3] = kVariants[v].f64[0] != nullptr;
   info[4] = kVariants[v].stages;
   info[5] = kVariants[v].fused;
   return true;
@@ -123,7 +134,7 @@ Tuning tuning_get() {
 heat_status tuning_set(const Tuning& t) {
   for (int p = 0; p < 3; ++p) {
     const int v = t.variant[p];
-    if (v < -1 || v >= kNumVariants || (v >= 0 && p == P_FP64 && !kVariants[v].f64))
+    if (v < -1 || v >= kNumVariants || (v >= 0 && p == P_FP64 && !kVariants[v].f64[0]))
       return set_error(HEAT_ERR_ARG, "tuning: bad variant %d for precision %d", v, p);
   }
   for (int p = 0; p < 3; ++p)
@@ -153,16 +164,7 @@ static TileFn update_kernel(int prec, int qpt) {
 // (cheb) a fused variant is replaced by the register-prefetch variant of the
 // same segment shape: the fused iteration has no place for the passes.
 static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int elem = E_Q1) {
-  if (elem == E_P1) {  // block tiles only: the warp variants are trilinear
-    KernelSet k = prec == P_FP64 ? make_set<P_FP64, 16, 16, E_P1>()
-                                 : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16, E_P1>()
-                                                            : make_set<P_FP32_PLAIN, 16, 16, E_P1>());
-    for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
-    const int qpt = t.pw_quads[prec];
-    k.pw_chunk = pw_chunk(qpt);
-    k.update = update_kernel(prec, qpt);
-    return k;
-  }
+  const int ei = elem == E_P1 ? 1 : 0;
   int variant = t.variant[prec];
   if (cheb && variant >= 0 && variant < kNumVariants && kVariants[variant].fused) {
     const WVariant& f = kVariants[variant];
@@ -173,19 +175,25 @@ static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int el
         alt = v;
     variant = alt >= 0 ? alt : 0;
   }
-  KernelSet k = prec == P_FP64 ? make_set<P_FP64, 16, 16>()
-                               : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16>()
-                                                          : make_set<P_FP32_PLAIN, 16, 16>());
+  KernelSet k;
+  if (elem == E_P1)
+    k = prec == P_FP64 ? make_set<P_FP64, 16, 16, E_P1>()
+                       : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16, E_P1>()
+                                                  : make_set<P_FP32_PLAIN, 16, 16, E_P1>());
+  else
+    k = prec == P_FP64 ? make_set<P_FP64, 16, 16>()
+                       : (prec == P_FP32_REFINED ? make_set<P_FP32_REFINED, 16, 16>()
+                                                  : make_set<P_FP32_PLAIN, 16, 16>());
   if (variant >= 0 && variant < kNumVariants) {
     const WVariant& v = kVariants[variant];
-    k.apply_w = prec == P_FP64 ? v.f64 : v.f32;
+    k.apply_w = prec == P_FP64 ? v.f64[ei] : v.f32[ei];
     if (k.apply_w) {
       k.wsx = v.sx;
       k.wny = v.ny;
       k.wwarps = v.warps;
       k.apply_w_smem = prec == P_FP64 ? v.smem64 : v.smem32;
       k.fused = v.fused;
-      k.cheb_w = prec == P_FP64 ? v.cheb64 : v.cheb32;
+      k.cheb_w = prec == P_FP64 ? v.cheb64[ei] : v.cheb32[ei];
       if (k.apply_w_smem > 0)
         cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
     }
@@ -887,7 +895,7 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
   double best_t = 1e300;
   heat_status st = HEAT_OK;
   for (int v = -1; v < kNumVariants && st == HEAT_OK; ++v) {
-    if (v >= 0 && prec == P_FP64 && !kVariants[v].f64) continue;
+    if (v >= 0 && prec == P_FP64 && !kVariants[v].f64[0]) continue;
     for (int si = 0; si < (v < 0 ? 1 : 4) && st == HEAT_OK; ++si) {
       Tuning t = base;
       t.variant[prec] = v;

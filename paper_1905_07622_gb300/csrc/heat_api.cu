@@ -341,6 +341,14 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   for (int f = 0; f < 6; ++f) d.g[f] = b.dirichlet_value[f];
   const double hx = mesh->extent[0] / mesh->nx, hy = mesh->extent[1] / mesh->ny, hz = mesh->extent[2] / mesh->nz;
   element_classes(hx, hy, hz, d.mhat, d.khat);
+  {
+    const double vol = hx * hy * hz / 6.0;
+    d.p1c[0] = vol / 20.0;
+    d.p1c[1] = vol / (hx * hx);
+    d.p1c[2] = vol / (hy * hy);
+    d.p1c[3] = vol / (hz * hz);
+    for (int t = 0; t < 4; ++t) d.p1c_f[t] = (float)d.p1c[t];
+  }
   walsh_eigenvalues(hx, hy, hz, d.lam_m, d.lam_k);
   for (int p = 0; p < 8; ++p) {
     d.mhat_f[p] = (float)d.mhat[p];

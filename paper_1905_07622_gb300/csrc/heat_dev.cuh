@@ -138,6 +138,10 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   // FP64 and FP32 copies.
   const double* p1w;
   const float* p1w_f;
+  // their structure for the box-centred form (op_warp.cuh): V / 20 and
+  // V / h_a^2 (a = x, y, z) with V = hx hy hz / 6
+  double p1c[4];
+  float p1c_f[4];
   double* partial;            // 2 per tile
   int* iters_log;             // CG iterations of each step
   int iters_log_len;

@@ -12,6 +12,9 @@ namespace heat {
 
 // ------------------------------------------------------------ the operator
 
+template <class T> __device__ __forceinline__ const T* p1_consts(const SimDev& s);
+template <> __device__ __forceinline__ const double* p1_consts<double>(const SimDev& s) { return s.p1c; }
+template <> __device__ __forceinline__ const float* p1_consts<float>(const SimDev& s) { return s.p1c_f; }
 template <class T> __device__ __forceinline__ const T* p1_weights(const SimDev& s);
 template <> __device__ __forceinline__ const double* p1_weights<double>(const SimDev& s) { return s.p1w; }
 template <> __device__ __forceinline__ const float* p1_weights<float>(const SimDev& s) { return s.p1w_f; }

@@ -355,16 +355,115 @@ __device__ __forceinline__ void warp_tile_march(const LaneGeo<NY>& lg, const Sim
   }
 }
 
-// The register-prefetch form with functor loads (see RegSrc).
-template <class T, int SX, int NY, class Coef, class Fetch, class Value, class Out>
-__device__ __forceinline__ void warp_tile_op(const Geo& g, const SimDev& s, const Coef* __restrict__ coef, bool active,
-                                             int i0, int j0, int k0, int tzl, T sa, T sb, bool mask, Fetch&& fetch,
-                                             Value&& value, Out&& out) {
+// The same contract on six-tetrahedra boxes (heat.h HEAT_ELEM_P1). Each lane
+// computes its box column's boxes row by row from the staged levels L-1 and
+// L of its own column and of its right neighbour (one shuffle per row), with
+// the split's structure instead of an 8x8 matrix:
+//  - mass: each tetrahedron t adds V/20 (x_c + s_t) at its corners, s_t the
+//    sum of its four values; a box corner c lies in n_c tetrahedra (6 for
+//    corners 0 and 7, 2 for the others);
+//  - stiffness: sum over the 12 box edges of w_e V/h_a^2 (x_i - x_j)^2, w_e
+//    the number of tetrahedra that step along the edge: 2, 1, 1, 2 for the
+//    edges of axis a leaving corners 0, the two one-axis corners and the
+//    two-axis corner (the path gradients are axis-aligned).
+// About 90 operations per box with every weight in registers. A node sums its
+// <= 8 boxes' contributions in a fixed order: the upper corners of the layer
+// below (carried in registers), then this layer's lower corners, the left
+// neighbour's through one shuffle per row.
+template <class T, int SX, int NY, class Src, class Out>
+__device__ __forceinline__ void warp_tile_march_p1(const LaneGeo<NY>& lg, const SimDev& s, Src& src, int tzl, T sa,
+                                                   T sb, Out&& out) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int NR = NY + 2;  // staged rows
+  constexpr int NF = NY + 1;  // box rows
+  const T mw = sa * p1_consts<T>(s)[0];  // V / 20 and V / h_a^2, V = hx hy hz / 6
+  const T kwx = sb * p1_consts<T>(s)[1], kwy = sb * p1_consts<T>(s)[2], kwz = sb * p1_consts<T>(s)[3];
+  src.prologue(lg, tzl);
+  T prv[NR], prvR[NR], carry[NY];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) prv[r] = prvR[r] = T(0);
+#pragma unroll
+  for (int r = 0; r < NY; ++r) carry[r] = T(0);
+  const int k0 = src.k0;
+  for (int t = 0; t <= tzl + 1; ++t) {
+    const int L = k0 - 1 + t;
+    T cur[NR], curR[NR];
+    src.level(lg, t, tzl, cur);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) curR[r] = __shfl_down_sync(FULL, cur[r], 1, SX);
+    if (t >= 1) {
+      // boxes (lane column, row r, layer L-1): lower corners to level L-1,
+      // upper corners to level L; cx = 1 corners belong to the right lane
+      T lo0[NF], lo2[NF], lo1[NF], lo3[NF], up4[NF], up6[NF], up5[NF], up7[NF];
+#pragma unroll
+      for (int r = 0; r < NF; ++r) {
+        const auto cf = src.coef_row(t, r);
+        const T x0 = prv[r], x1 = prvR[r], x2 = prv[r + 1], x3 = prvR[r + 1];
+        const T x4 = cur[r], x5 = curR[r], x6 = cur[r + 1], x7 = curR[r + 1];
+        const T s07 = x0 + x7;
+        const T t1 = s07 + x1 + x3, t2 = s07 + x1 + x5, t3 = s07 + x2 + x3;
+        const T t4 = s07 + x2 + x6, t5 = s07 + x4 + x5, t6 = s07 + x4 + x6;
+        const T S6 = ((t1 + t2) + (t3 + t4)) + (t5 + t6);
+        const T m = mw * cf.x;
+        const T ax = kwx * cf.y, ay = kwy * cf.y, az = kwz * cf.y;
+        const T e01 = T(2) * ax * (x0 - x1), e23 = ax * (x2 - x3), e45 = ax * (x4 - x5), e67 = T(2) * ax * (x6 - x7);
+        const T e02 = T(2) * ay * (x0 - x2), e13 = ay * (x1 - x3), e46 = ay * (x4 - x6), e57 = T(2) * ay * (x5 - x7);
+        const T e04 = T(2) * az * (x0 - x4), e15 = az * (x1 - x5), e26 = az * (x2 - x6), e37 = T(2) * az * (x3 - x7);
+        lo0[r] = m * (T(6) * x0 + S6) + e01 + e02 + e04;
+        lo1[r] = m * (T(2) * x1 + t1 + t2) - e01 + e13 + e15;
+        lo2[r] = m * (T(2) * x2 + t3 + t4) + e23 - e02 + e26;
+        lo3[r] = m * (T(2) * x3 + t1 + t3) - e23 - e13 + e37;
+        up4[r] = m * (T(2) * x4 + t5 + t6) + e45 + e46 - e04;
+        up5[r] = m * (T(2) * x5 + t2 + t5) - e45 + e57 - e15;
+        up6[r] = m * (T(2) * x6 + t4 + t6) + e67 - e46 - e26;
+        up7[r] = m * (T(6) * x7 + S6) - e67 - e57 - e37;
+      }
+      src.after_elements(lg, t, tzl);
+      const int lv = L - 1;
+      const bool lvin = lv <= lg.gnz;
+      const bool dzl = (lg.dz0 && lv == 0) || (lg.dz1 && lv == lg.gnz);
+#pragma unroll
+      for (int r = 1; r <= NY; ++r) {
+        // node row r: boxes r (cy = 0) and r - 1 (cy = 1)
+        const T from_left_lo = __shfl_up_sync(FULL, lo1[r] + lo3[r - 1], 1, SX);
+        const T from_left_up = __shfl_up_sync(FULL, up5[r] + up7[r - 1], 1, SX);
+        const T y = ((carry[r - 1] + lo0[r]) + lo2[r - 1]) + from_left_lo;
+        carry[r - 1] = (up4[r] + up6[r - 1]) + from_left_up;
+        const int m = lg.nbase + r * lg.px + lv * lg.pxy;
+        if (t >= 2 && lg.out_lane && lvin && ((lg.rin >> r) & 1u) && HEAT_INDEX_OK(lg.sc, m, lg.nn)) {
+          const bool dir = ((lg.rdxy >> r) & 1u) || dzl;
+          out(m, dir, y, prv[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      prv[r] = cur[r];
+      prvR[r] = curR[r];
+    }
+  }
+}
+
+// The march of element type E.
+template <int E, class T, int SX, int NY, class Src, class Out>
+__device__ __forceinline__ void warp_march_e(const LaneGeo<NY>& lg, const SimDev& s, Src& src, int tzl, T sa, T sb,
+                                             Out&& out) {
+  if constexpr (E == E_P1)
+    warp_tile_march_p1<T, SX, NY>(lg, s, src, tzl, sa, sb, out);
+  else
+    warp_tile_march<T, SX, NY>(lg, s, src, tzl, sa, sb, out);
+}
+
+// The register-prefetch form with functor loads (see RegSrc), for element E.
+template <int E, class T, int SX, int NY, class Coef, class Fetch, class Value, class Out>
+__device__ __forceinline__ void warp_tile_op_e(const Geo& g, const SimDev& s, const Coef* __restrict__ coef,
+                                               bool active, int i0, int j0, int k0, int tzl, T sa, T sb, bool mask,
+                                               Fetch&& fetch, Value&& value, Out&& out) {
   const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, i0, j0, mask, s.sc);
   using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
   RegSrc<T, NY, CoefT, typename std::remove_reference<Fetch>::type, typename std::remove_reference<Value>::type> src(
       coef, fetch, value, k0);
-  warp_tile_march<T, SX, NY>(lg, s, src, tzl, sa, sb, out);
+  warp_march_e<E, T, SX, NY>(lg, s, src, tzl, sa, sb, out);
 }
 
 }  // namespace heat

@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
 // level ahead into registers; STAGES >= 2 stages each thread's loads through
 // its own cp.async ring of that many levels in dynamic shared memory
 // (async_stage_bytes per thread). MINB blocks per SM bound the registers.
-template <class T, int SX, int NY, int WARPS, int STAGES, int MINB>
+template <class T, int SX, int NY, int WARPS, int STAGES, int MINB, int E = E_Q1>
 __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* __restrict__ sims,
                                                             const int2* __restrict__ work,
                                                             const int* __restrict__ nwork_p) {
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
       acc += v * qv;
     };
     if constexpr (STAGES == 0) {
-      warp_tile_op<T, SX, NY>(
+      warp_tile_op_e<E, T, SX, NY>(
           g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
           (T)s.theta, true,
           [&](int m, bool live) -> DirRaw<T> {
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
       const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
       AsyncSrc<T, NY, STAGES, CoefT> src(pinv, r, rs ? nullptr : dold, IterVecs<T>::coef(s), beta, stage_smem,
                                          (int)blockDim.x, (int)threadIdx.x, tz * s.w_tz);
-      warp_tile_march<T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
+      warp_march_e<E, T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
     }
     const T accv[1] = {acc};
     double tot[1];
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(SX* SY) k_cheb(const SimDev* __restrict__ sims
 }
 
 // Warp-segment form of k_cheb (the register-prefetch march of k_apply_dot_w).
-template <class T, int SX, int NY, int WARPS, int MINB>
+template <class T, int SX, int NY, int WARPS, int MINB, int E = E_Q1>
 __global__ void __launch_bounds__(32 * WARPS, MINB) k_cheb_w(const SimDev* __restrict__ sims,
                                                               const int2* __restrict__ work,
                                                               const int* __restrict__ nwork_p) {
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_cheb_w(const SimDev* __res
     const bool active = tile < s.w_ntiles;
     const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
     ChebPass<T> ps(s, c.cheb_k);
-    warp_tile_op<T, SX, NY>(
+    warp_tile_op_e<E, T, SX, NY>(
         g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt, (T)s.theta,
         true, [&](int m, bool live) { return ps.fetch(m, live); }, [&](const ChRaw<T>& v) { return ps.value(v); },
         [&](int m, bool dir, T y, T v) { ps.out(m, dir, y, v); });
@@ -910,7 +910,7 @@ struct CgSrc {
 // alpha = r.u / w.u without updating. Same work lists and results contract as
 // k_apply_dot_w; the convergence tests of k_update (gamma is the r.P^-1 r of
 // Algorithm 1).
-template <int SX, int NY, int WARPS, int MINB>
+template <int SX, int NY, int WARPS, int MINB, int E = E_Q1>
 __global__ void __launch_bounds__(32 * WARPS, MINB) k_cg_iter(const SimDev* __restrict__ sims,
                                                                const int2* __restrict__ work,
                                                                const int* __restrict__ nwork_p) {
@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_cg_iter(const SimDev* __re
     float* __restrict__ wout = mode == 0 ? s.wc32[slot] : s.wc32[nslot];
     float del = 0.f;
     const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
-    warp_tile_march<float, SX, NY>(lg, s, src, s.w_tz, (float)s.inv_dt, (float)s.theta,
+    warp_march_e<E, float, SX, NY>(lg, s, src, s.w_tz, (float)s.inv_dt, (float)s.theta,
                                    [&](int m, bool dir, float y, float v) {
                                      const float wv = dir ? 0.f : y;
                                      wout[m] = wv;

@@ -1,5 +1,6 @@
-"""Kernel tuning: every apply variant and segment size against the oracle,
-bitwise batch equality under a non-default table, and the autotuner.
+"""Kernel tuning: every apply variant and segment size against the oracle
+(trilinear and six-tetrahedra boxes), bitwise batch equality under a
+non-default table, and the autotuner.
 
 The tuning table picks which warp-segment apply kernel runs and how large
 its tiles are; every choice must give the same step solutions (within the
@@ -68,6 +69,27 @@ def test_every_variant_and_segment_size_matches_oracle(precision, tol):
         for n in range(1, p.nsteps + 1):
             err = np.linalg.norm(us[n - 1] - ref.u[n]) / np.linalg.norm(ref.u[n])
             assert err <= tol, (v, seg, quads, n, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32_refined", 1e-8)])
+def test_every_variant_on_six_tetrahedra_boxes(precision, tol):
+    """The box-centred P1 march under every load policy (register prefetch,
+    cp.async ring, the fused iteration) and the P1 block tiles."""
+    import paper_1905_07622_gb300 as hg
+    p = _problem()
+    p.element = "p1"
+    ref = pins.oracle_steps(p)
+    pid = hg.PRECISIONS[precision]
+    for v in _variants(precision == "fp64"):
+        for seg in ([512] if v < 0 else [64, 2048]):
+            table = hg.heat_tuning_get()
+            table["variant"][pid] = v
+            table["seg_nodes"][0] = seg
+            hg.heat_tuning_set(table["variant"], table["seg_nodes"], table["pw_quads"])
+            us = _solve(p, precision)
+            for n in range(1, p.nsteps + 1):
+                err = np.linalg.norm(us[n - 1] - ref.u[n]) / np.linalg.norm(ref.u[n])
+                assert err <= tol, (v, seg, n, err)
 
 
 def test_batch_bitwise_equal_to_alone_under_a_tuned_table():

@@ -196,8 +196,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+def current_variant(hg, precision: str):
+    """(segment width, rows, warps, stages, fused) of the apply the current table runs, or None (block tiles)."""
+    v = hg.heat_tuning_get()["variant"][hg.PRECISIONS[precision]]
+    if v < 0:
+        return None
+    i = hg.heat_tuning_variant(v)
+    return [i["seg_width"], i["rows"], i["warps"], i["stages"], int(i["fused"])]
+
+
+def ncu_traffic(kernel_key: str, variant=None):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel source and the apply variant the table runs now."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -213,6 +223,8 @@ def ncu_traffic(kernel_key: str):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest() != d.get("sha256"):
         return None  # kernel changed since the counters were taken
+    if variant is not None and d.get("variant") != variant:
+        return None  # the counters are another variant's
     return d.get("dram_bytes_per_launch")
 
 
@@ -352,7 +364,8 @@ def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tunin
                 "kernel_launches": stats[0]["kernel_launches"], "tuning": tuning,
                 "roofline": {"bound": "hbm", "kernel": "k_apply_dot<float>", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": ncu_traffic("k_apply_dot<float>@lognormal_batch_256x40"),
+                             "traffic": ncu_traffic("k_apply_dot<float>@lognormal_batch_256x40",
+                                                   current_variant(hg, "fp32_refined")),
                              "ms_per_launch": prof["ms_apply"],
                              "algorithmic_bytes_per_launch": prof["bytes_apply"],
                              "update_kernel": {"ms_per_launch": prof["ms_update"],
@@ -402,7 +415,8 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
                           "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec, "kernel_tuning": tuning,
                           "apply": {"ms_per_launch": prof["ms_apply"], "achieved_gbs": achieved, "peak_gbs": peak,
                                     "frac": achieved / peak, "algorithmic_bytes_per_launch": prof["bytes_apply"],
-                                    "traffic": ncu_traffic("k_apply_dot<float>@layered_cube_200")
+                                    "traffic": ncu_traffic("k_apply_dot<float>@layered_cube_200",
+                                                                           current_variant(hg, "fp32_refined"))
                                     if precision == "fp32_refined" else None},
                           "update": {"ms_per_launch": prof["ms_update"],
                                      "achieved_gbs": prof["bytes_update"] / (prof["ms_update"] * 1e-3) / 1e9
@@ -438,6 +452,27 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
                                    "interval": [lo, hi], "status": st["status"],
                                    "final_field_rel_diff_vs_jacobi": float(np.linalg.norm(uc - u32) / np.linalg.norm(u32))}
         out["chebyshev_fp32_refined"] = {"ratio": cheb_ratio, **legs}
+    # the laminate on §4.1's own element (six tetrahedra per box), same steps and table
+    pp = W.layered_cube(nsteps=nsteps)
+    pp.element = "p1"
+    if tuned32 is not None:
+        hg.heat_tuning_set(tuned32["table"]["variant"], tuned32["table"]["seg_nodes"], tuned32["table"]["pw_quads"])
+    with hg.Simulation.from_problem(pp, precision="fp32_refined", stream=stream.cuda_stream) as s:
+        s.step(1)
+        hg.heat_set_state(s.sim, pp.u0, s.n_nodes)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = s.step(nsteps)
+        e.record(stream)
+        e.synchronize()
+        sec = a.elapsed_time(e) / 1e3
+        up = s.state()
+    out["six_tetrahedra_fp32_refined"] = {
+        "ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"], "status": st["status"],
+        "dof_cg_iters_per_s": pp.n_nodes * st["iters"] / sec,
+        "final_field_rel_diff_vs_trilinear": float(np.linalg.norm(up - u32) / np.linalg.norm(u32))}
     return out
 
 
@@ -692,7 +727,7 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
     kernel_key = f"k_apply_dot<{'double' if args.precision == 'fp64' else 'float'}>@inclusions_cube_100"
-    traffic = ncu_traffic(kernel_key)
+    traffic = ncu_traffic(kernel_key, current_variant(hg, args.precision))
 
     batched = serving = layered = mh = p1 = None
     if rank == 0 and args.batch_sims > 0:

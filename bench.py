@@ -476,7 +476,7 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
     return out
 
 
-def run_p1(hg, torch, nsteps: int, stream):
+def run_p1(hg, torch, nsteps: int, stream, table=None):
     """The inclusions workload on six-tetrahedra boxes (§4.1's element: 6
     million linear tetrahedra on the 100^3 grid, 1,030,301 DOF), FP32-refined,
     first `nsteps` of its 300 steps; plus the P1 apply kernel timed alone after
@@ -487,6 +487,9 @@ def run_p1(hg, torch, nsteps: int, stream):
                        f"first {nsteps} of its 300 steps, FP32-refined, rtol 1e-10"}
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     peak, _ = measured_peaks()
+    if table is not None:  # the headline's kernel table (later legs retune for their own sizes)
+        hg.heat_tuning_set(table["variant"], table["seg_nodes"], table["pw_quads"])
+    out["kernel_table"] = hg.heat_tuning_get()
     for element in ("p1", "q1"):
         p = W.inclusions_cube(nsteps=nsteps)
         p.element = element
@@ -738,7 +741,7 @@ def main():
     if rank == 0 and args.mh_chains > 0:
         mh = run_mh(hg, torch, args.mh_chains, args.mh_iters, stream)
     if rank == 0 and args.p1_steps > 0:
-        p1 = run_p1(hg, torch, args.p1_steps, stream)
+        p1 = run_p1(hg, torch, args.p1_steps, stream, tuning["table"] if tuning else None)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
 

@@ -762,6 +762,7 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_of_nominal_7900_gbs": achieved / 7900.0,
                          "kernel": kernel_key.split("@")[0], "peak_kind": f"{peak_kind} HBM copy (burst)",
                          "ms_per_launch": prof["ms_apply"], "algorithmic_bytes_per_launch": prof["bytes_apply"],
                          "update_kernel": {"ms_per_launch": prof["ms_update"], "algorithmic_bytes_per_launch": prof["bytes_update"],

@@ -174,10 +174,10 @@ __host__ __device__ constexpr int async_stage_bytes() {
 }
 
 // The direction-fused apply's loads (P^-1, r, d_old per node; (rho_c, k) per
-// element) staged through a per-thread ring of S stages; pinv = nullptr is a
-// unit scale, dold = nullptr a restart. Stage t holds node level k0-1+t and
-// element layer k0-2+t. Layout: planes of nt values (one per thread of the
-// block), so a warp's accesses are conflict-free.
+// element) staged through a per-thread ring of S stages; dold = nullptr is a
+// restart. Stage t holds node level k0-1+t and element layer k0-2+t. Layout:
+// planes of nt values (one per thread of the block), so a warp's accesses are
+// conflict-free.
 template <class T, int NY, int S, class Coef>
 struct AsyncSrc {
   static constexpr int NR = NY + 2, NF = NY + 1;
@@ -212,7 +212,7 @@ struct AsyncSrc {
     for (int row = 0; row < NR; ++row) {
       const bool live = ((lv >> row) & 1u) && HEAT_INDEX_OK(lg.sc, off + row * lg.px, lg.nn);
       const int m = live ? off + row * lg.px : 0;
-      if (pinv) cp_async<sizeof(T)>(node_slot(st, row, 0), pinv + m, live);
+      cp_async<sizeof(T)>(node_slot(st, row, 0), pinv + m, live);
       cp_async<sizeof(T)>(node_slot(st, row, 1), r + m, live);
       if (dold) cp_async<sizeof(T)>(node_slot(st, row, 2), dold + m, live);
     }
@@ -241,7 +241,7 @@ struct AsyncSrc {
     const int st = t % S;
 #pragma unroll
     for (int row = 0; row < NR; ++row) {
-      const T p = pinv ? *node_slot(st, row, 0) : T(1), rv = *node_slot(st, row, 1);
+      const T p = *node_slot(st, row, 0), rv = *node_slot(st, row, 1);
       const T d = dold ? *node_slot(st, row, 2) : T(0);
       v[row] = p * rv + beta * d;
     }

@@ -524,10 +524,9 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
     if (c.phase != PH_ITER) continue;
     const Geo g(s);
     const TileCoords tc = tile_coords<SX, SY>(s, wi.y);
-    // d = P^-1 r + beta d_old, or z + beta d_old after Chebyshev passes (no scale)
-    const bool ch = s.cheb_m >= 2;
-    const T* __restrict__ r = ch ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);
-    const T* __restrict__ pinv = ch ? nullptr : IterVecs<T>::pinv(s);
+    // d = P^-1 r + beta d_old; after Chebyshev passes r is their P z, so d = z + beta d_old
+    const T* __restrict__ r = s.cheb_m >= 2 ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);
+    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
     const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
     T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
     T* __restrict__ q = IterVecs<T>::q(s);
@@ -539,7 +538,7 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
         g, s, IterVecs<T>::coef(s), tc.i0, tc.j0, tc.k0, tc.nzt, (T)s.inv_dt, (T)s.theta, true, sh,
         [&](int m, bool live) -> DirRaw<T> {
           if (!live) return {T(0), T(0), T(0)};
-          return {pinv ? pinv[m] : T(1), r[m], rs ? T(0) : dold[m]};
+          return {pinv[m], r[m], rs ? T(0) : dold[m]};
         },
         [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; },
         [&](int m, bool dir, T y, T v) {
@@ -594,9 +593,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
     const int tile = wi.y * SPC + (int)threadIdx.x / SX;
     const bool active = tile < s.w_ntiles;
     const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
-    const bool ch = s.cheb_m >= 2;  // see k_apply_dot
-    const T* __restrict__ r = ch ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);
-    const T* __restrict__ pinv = ch ? nullptr : IterVecs<T>::pinv(s);
+    const T* __restrict__ r = s.cheb_m >= 2 ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);  // see k_apply_dot
+    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
     const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
     T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
     T* __restrict__ q = IterVecs<T>::q(s);
@@ -615,7 +613,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
           (T)s.theta, true,
           [&](int m, bool live) -> DirRaw<T> {
             if (!live) return {T(0), T(0), T(0)};
-            return {pinv ? pinv[m] : T(1), r[m], rs ? T(0) : dold[m]};
+            return {pinv[m], r[m], rs ? T(0) : dold[m]};
           },
           [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
     } else {
@@ -655,9 +653,11 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
 //   dd_k = rho_k rho_{k-1} dd_{k-1} + (2 rho_k / delta) D^-1 res_k,
 //   z_{k+1} = z_k + dd_k.
 // Pass k stages dd_{k-1} (formed from r on pass 1) through the operator and
-// updates its own nodes; dd_k lives in slot k & 1. The last pass writes only
-// z_m and sums r^T z_m, which becomes delta (and beta = delta / delta_old)
-// of the CG iteration. Dirichlet rows and columns are masked as in the apply.
+// updates its own nodes; dd_k lives in slot k & 1. The last pass sums
+// r^T z_m, which becomes delta (and beta = delta / delta_old) of the CG
+// iteration, and stores P z_m (z_m divided by P^-1), so that the apply forms
+// d = P^-1 (P z) + beta d_old = z + beta d_old with its Jacobi staging
+// unchanged (to rounding). Dirichlet rows and columns are masked as in the apply.
 template <class T>
 struct ChRaw {
   T a, b;
@@ -702,13 +702,15 @@ struct ChebPass {
       return;
     }
     const T rr = (first || last) ? r[m] : T(0);
+    const T p = pinv[m];
     const T rk = (first ? rr : res[m]) - y;
-    const T dk = c1 * v + c2 * (pinv[m] * rk);
+    const T dk = c1 * v + c2 * (p * rk);
     const T zn = (first ? v : z[m]) + dk;
-    z[m] = zn;
     if (last) {
       acc += rr * zn;
+      z[m] = zn / p;
     } else {
+      z[m] = zn;
       res[m] = rk;
       ddout[m] = dk;
     }

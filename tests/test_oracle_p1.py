@@ -140,3 +140,18 @@ def test_transient_energy_balance_and_spectral_bound():
     D = S.pinv_f
     lam = np.linalg.eigvals(D[:, None] * S.A_ff.toarray()).real
     assert lam.max() <= precond.element_lam_max(p) * (1 + 1e-12)
+
+
+def test_single_loaded_quad_shares():
+    # one loaded boundary quad: its two triangles (split along the lower-to-upper
+    # diagonal) give the diagonal's ends q A / 3 and the other corners q A / 6
+    nx, ny, nz, ext = 4, 3, 5, (2.0, 3.0, 1.0)
+    hx, hy, hz = fem.spacing(nx, ny, nz, ext)
+    q = np.zeros(nx * nz)
+    q[2 + nx * 3] = 1.5  # face y=0, quad (i=2, k=3)
+    F = p1.face_load_elements(nx, ny, nz, ext, 2, q)
+    A = hx * hz
+    share = {(2, 3): 1 / 3, (3, 4): 1 / 3, (3, 3): 1 / 6, (2, 4): 1 / 6}
+    for (i, k), w in share.items():
+        assert math.isclose(F[fem.node_id(nx, ny, i, 0, k)], 1.5 * A * w, rel_tol=1e-13)
+    assert np.count_nonzero(F) == 4

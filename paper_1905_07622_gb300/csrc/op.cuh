@@ -6,6 +6,7 @@
 
 #include <type_traits>
 
+#include "df.cuh"
 #include "heat_dev.cuh"
 
 namespace heat {
@@ -15,9 +16,14 @@ namespace heat {
 template <class T> __device__ __forceinline__ const T* p1_consts(const SimDev& s);
 template <> __device__ __forceinline__ const double* p1_consts<double>(const SimDev& s) { return s.p1c; }
 template <> __device__ __forceinline__ const float* p1_consts<float>(const SimDev& s) { return s.p1c_f; }
-template <class T> __device__ __forceinline__ const T* p1_weights(const SimDev& s);
+// Storage type of the P1 box matrices for arithmetic type T (double-float
+// operators read the FP64 copy).
+template <class T> struct P1W { using type = T; };
+template <> struct P1W<DF> { using type = double; };
+template <class T> __device__ __forceinline__ const typename P1W<T>::type* p1_weights(const SimDev& s);
 template <> __device__ __forceinline__ const double* p1_weights<double>(const SimDev& s) { return s.p1w; }
 template <> __device__ __forceinline__ const float* p1_weights<float>(const SimDev& s) { return s.p1w_f; }
+template <> __device__ __forceinline__ const double* p1_weights<DF>(const SimDev& s) { return s.p1w; }
 
 // The six-tetrahedra form of gather_apply: node (i,j,k) is local corner c of
 // each of its <= 8 boxes, and row c of the box matrices M', K' couples it to
@@ -119,6 +125,7 @@ struct Geo {
 template <class T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<DF> { using type = DF2; };
 
 template <class T, int SX, int SY>
 struct TileSmem {
@@ -129,9 +136,11 @@ struct TileSmem {
 template <class T> __device__ __forceinline__ T lam_m(const SimDev& s, int w);
 template <> __device__ __forceinline__ double lam_m<double>(const SimDev& s, int w) { return s.lam_m[w]; }
 template <> __device__ __forceinline__ float lam_m<float>(const SimDev& s, int w) { return s.lam_m_f[w]; }
+template <> __device__ __forceinline__ DF lam_m<DF>(const SimDev& s, int w) { return DF(s.lam_m[w]); }
 template <class T> __device__ __forceinline__ T lam_k(const SimDev& s, int w);
 template <> __device__ __forceinline__ double lam_k<double>(const SimDev& s, int w) { return s.lam_k[w]; }
 template <> __device__ __forceinline__ float lam_k<float>(const SimDev& s, int w) { return s.lam_k_f[w]; }
+template <> __device__ __forceinline__ DF lam_k<DF>(const SimDev& s, int w) { return DF(s.lam_k[w]); }
 
 // A node column (i, j) of a tile: node index base (level 0), whether it lies
 // inside the mesh, and whether an x or y Dirichlet face contains it.
@@ -203,8 +212,8 @@ __device__ __forceinline__ void tile_op(const Geo& g, const SimDev& s, const Coe
   using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
   auto coef_of = [&](int E) -> CoefT {  // element (i, j, E); zero outside the mesh
     CoefT c;
-    c.x = T(0);
-    c.y = T(0);
+    c.x = 0;
+    c.y = 0;
     if (elem_col && E >= 0 && E < gnz && HEAT_INDEX_OK(s.sc, ebase + estride * E, ne_all))
       c = coef[ebase + estride * E];  // int: N < 2^31 per simulation
     return c;

@@ -44,7 +44,7 @@ __device__ __forceinline__ void tile_op_p1(const Geo& g, const SimDev& s, const 
   const bool lastx = lx == SX - 1, lasty = ly == SY - 1;
   const bool elem_col = i >= 0 && j >= 0 && i < g.nx && j < g.ny;
   const Col c00(g, i, j), c10(g, i + 1, j), c01(g, i, j + 1), c11(g, i + 1, j + 1);
-  const T* w = p1_weights<T>(s);
+  const auto* w = p1_weights<T>(s);
   for (int t = (int)threadIdx.x; t < 64; t += (int)blockDim.x) {
     sh.wm[t] = sa * w[t];
     sh.wk[t] = sb * w[64 + t];
@@ -72,8 +72,8 @@ __device__ __forceinline__ void tile_op_p1(const Geo& g, const SimDev& s, const 
   using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(coef[0])>::type>::type;
   auto coef_of = [&](int E) -> CoefT {  // element (i, j, E); zero outside the mesh
     CoefT c;
-    c.x = T(0);
-    c.y = T(0);
+    c.x = 0;
+    c.y = 0;
     if (elem_col && E >= 0 && E < gnz && HEAT_INDEX_OK(s.sc, ebase + estride * E, ne_all))
       c = coef[ebase + estride * E];
     return c;

@@ -249,10 +249,17 @@ struct D2 {
   double a, b;
 };
 
+// Arithmetic of the operator passes of k_open: FP64 on the FP64 path. On the
+// FP32 paths the passes form the refinement's right-hand side and true
+// residual, and run in double-float (df.cuh): about 48 bits, several times the
+// FP64 pass's speed on this GPU; the vectors and sums stay FP64.
+template <int P> using OpenT = typename std::conditional<P == P_FP64, double, DF>::type;
+
 template <int P, int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims, const int2* __restrict__ work,
                                                  const int* __restrict__ nwork_p) {
-  __shared__ OpSmem<E, double, SX, SY> sh;
+  using TO = OpenT<P>;
+  __shared__ OpSmem<E, TO, SX, SY> sh;
   __shared__ double red[3 * 32];
   __shared__ ItemCache cache;
   int cur = -1;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
     const double* __restrict__ pinv = s.pinv;
     double* __restrict__ b = s.b;
     double part[3] = {0.0, 0.0, 0.0};  // r.P^-1 r (FP64), b.P^-1 b, r32.P^-1 r32
-    const double inv_dt = s.inv_dt, theta = s.theta;
+    const TO inv_dt = TO(s.inv_dt), theta = TO(s.theta), theta_m1 = TO(s.theta - 1.0);
     // the FP32 residual goes to the current slot of the fused iteration (slot 0 otherwise)
     float* __restrict__ r32out = s.fused ? s.rc32[c.cgs] : s.r32;
     // value of a Dirichlet node from its index (faces only, so rarely called)
@@ -297,10 +304,11 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       const double* __restrict__ y1 = s.yv[c.iu1];
       const double* __restrict__ y2 = s.yv[c.iu2];
       // pass 1: b = L u^{n-1} + F^n - A_{.D} g (free rows), g (Dirichlet rows)
-      tile_op_e<E, double, SX, SY>(
-          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta - 1.0, false, sh,
+      tile_op_e<E, TO, SX, SY>(
+          g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta_m1, false, sh,
           [&](int m, bool live) -> double { return live ? u1[m] : 0.0; }, ident,
-          [&](int m, bool dir, double y, double v) {
+          [&](int m, bool dir, TO yo, TO) {
+            const double y = to_d(yo);
             if (dir) {
               b[m] = dval(m);
               if (use_y) {
@@ -311,7 +319,8 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
               const double bn = y + (flux_on ? F[m] : 0.0) - lift[m];
               b[m] = bn;
               part[1] += bn * bn * pinv[m];
-              if (use_y) {  // v = U^{n-1}_m
+              if (use_y) {
+                const double v = u1[m];  // the staged input, read back in FP64
                 x[m] = hp ? 2.0 * v - u2[m] : v;
                 const double rn = bn - (hp ? 2.0 * y1[m] - y2[m] : y1[m]);
                 const float r32 = (float)rn;
@@ -322,19 +331,20 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
             }
           });
       // pass 2: x0 = 2u^{n-1} - u^{n-2} (u^{n-1} on the first step), r = b - A' x0
-      if (!use_y) tile_op_e<E, double, SX, SY>(
+      if (!use_y) tile_op_e<E, TO, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> D2 {
             if (!live) return {0.0, 0.0};
             return {u1[m], hp ? u2[m] : u1[m]};
           },
           [](const D2& r) { return 2.0 * r.a - r.b; },
-          [&](int m, bool dir, double y, double v) {
+          [&](int m, bool dir, TO yo, TO) {
+            const double y = to_d(yo);
             double rn = 0.0;
             if (dir) {
               x[m] = dval(m);
             } else {
-              x[m] = v;
+              x[m] = hp ? 2.0 * u1[m] - u2[m] : u1[m];  // the staged input, formed again in FP64
               rn = b[m] - y;
             }
             if (P == P_FP64) {
@@ -352,19 +362,20 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
       double* __restrict__ xa = s.vec64[c.ixa];
       double* __restrict__ ya = s.yv[c.ixa];  // A' x64, used by the next step if this one closes
       const float* __restrict__ e32 = s.e32;
-      tile_op_e<E, double, SX, SY>(
+      tile_op_e<E, TO, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> D2 {
             if (!live) return {0.0, 0.0};
             return {x[m], (double)e32[m]};
           },
           [](const D2& r) { return r.a + r.b; },
-          [&](int m, bool dir, double y, double v) {
+          [&](int m, bool dir, TO yo, TO) {
+            const double y = to_d(yo);
             double rn = 0.0;
             if (dir) {
               xa[m] = dval(m);
             } else {
-              xa[m] = v;
+              xa[m] = x[m] + (double)e32[m];  // the staged input, formed again in FP64
               ya[m] = y;
               rn = b[m] - y;
             }
@@ -376,10 +387,11 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
     } else {  // PH_RESID (FP64): r = b - A' x, x already advanced by k_update
       const double* __restrict__ x = s.vec64[c.ix];
       double* __restrict__ r = s.r;
-      tile_op_e<E, double, SX, SY>(
+      tile_op_e<E, TO, SX, SY>(
           g, s, s.coef, tc.i0, tc.j0, tc.k0, tc.nzt, inv_dt, theta, true, sh,
           [&](int m, bool live) -> double { return live ? x[m] : 0.0; }, ident,
-          [&](int m, bool dir, double y, double) {
+          [&](int m, bool dir, TO yo, TO) {
+            const double y = to_d(yo);
             const double rn = dir ? 0.0 : b[m] - y;
             r[m] = rn;
             part[0] += rn * rn * pinv[m];
@@ -456,18 +468,19 @@ __global__ void __launch_bounds__(SX* SY) k_open(const SimDev* __restrict__ sims
 template <int SX, int SY, int E = E_Q1>
 __global__ void __launch_bounds__(SX* SY) k_product(const SimDev* __restrict__ sd, const double* __restrict__ u,
                                                      double* __restrict__ y, int ntx, int nty, int tz) {
-  __shared__ OpSmem<E, double, SX, SY> sh;
+  using TO = OpenT<P_FP32_REFINED>;  // the arithmetic of k_open's passes on the FP32 paths
+  __shared__ OpSmem<E, TO, SX, SY> sh;
   const SimDev& s = *sd;
   const Geo g(s);
   const int t = blockIdx.x;
   const int tx = t % ntx, rem = t / ntx, ty = rem % nty, tk = rem / nty;
   const int k0 = tk * tz;
   const int nzt = min(tz, s.nz + 1 - k0);
-  tile_op_e<E, double, SX, SY>(
-      g, s, s.coef, tx * (SX - 1), ty * (SY - 1), k0, nzt, s.inv_dt, s.theta, true, sh,
+  tile_op_e<E, TO, SX, SY>(
+      g, s, s.coef, tx * (SX - 1), ty * (SY - 1), k0, nzt, TO(s.inv_dt), TO(s.theta), true, sh,
       [&](int m, bool live) -> double { return live ? u[m] : 0.0; }, [](double v) { return v; },
-      [&](int m, bool dir, double yv, double) {
-        if (!dir) y[m] = yv;
+      [&](int m, bool dir, TO yv, TO) {
+        if (!dir) y[m] = to_d(yv);
       });
 }
 

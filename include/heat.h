@@ -60,7 +60,9 @@ typedef enum {
 
 typedef enum {
   HEAT_FP64 = 0,         /* operator, vectors and dots in FP64 */
-  HEAT_FP32_REFINED = 1, /* FP32 operator/vectors, FP64 dots, FP64 outer refinement */
+  HEAT_FP32_REFINED = 1, /* FP32 operator/vectors, FP64 dots; outer refinement
+                            on FP64 vectors, its residual operator in
+                            double-float (pairs of floats, ~48 bits) */
   HEAT_FP32_PLAIN = 2    /* FP32 operator/vectors, FP64 dots, no refinement */
 } heat_precision;
 

@@ -7,7 +7,8 @@ outside it.
   boundary box face;
 - patch tests of the assembled matrices: K 1 = 0, K u = 0 on interior rows
   for a linear u, u^T K u = |grad u|^2 vol, 1^T M 1 = vol and u^T M v equal
-  to the exact integral of two linear functions;
+  to the exact integral of two linear functions; interior rows of K equal
+  the seven-point finite-difference stencil;
 - boundary loads: total q * area, and the A/3, A/6 corner shares of the
   triangle split;
 - the transient's energy balance; the element spectral bound above the
@@ -155,3 +156,22 @@ def test_single_loaded_quad_shares():
     for (i, k), w in share.items():
         assert math.isclose(F[fem.node_id(nx, ny, i, 0, k)], 1.5 * A * w, rel_tol=1e-13)
     assert np.count_nonzero(F) == 4
+
+
+def test_assembled_stiffness_is_the_seven_point_laplacian():
+    # every box edge along axis a is used by 2 + 1 + 1 + 2 = 6 of the tetrahedra
+    # around it (V/h_a^2 each, V = hx hy hz / 6), so interior rows of K are the
+    # finite-difference stencil (hx hy hz / h_a^2) (-1, 2, -1) summed over axes
+    nx, ny, nz, ext = 5, 4, 6, (1.0, 0.6, 1.5)
+    h = fem.spacing(nx, ny, nz, ext)
+    K = p1.assemble(nx, ny, nz, ext, np.ones(nx * ny * nz), "K").tocsr()
+    vol = h[0] * h[1] * h[2]
+    for (i, j, k) in [(1, 1, 1), (2, 2, 3), (3, 1, 4)]:
+        n = fem.node_id(nx, ny, i, j, k)
+        row = K.getrow(n).toarray().ravel()
+        want = np.zeros_like(row)
+        want[n] = sum(2.0 * vol / h[a] ** 2 for a in range(3))
+        for a, (di, dj, dk) in enumerate([(1, 0, 0), (0, 1, 0), (0, 0, 1)]):
+            for sgn in (-1, 1):
+                want[fem.node_id(nx, ny, i + sgn * di, j + sgn * dj, k + sgn * dk)] = -vol / h[a] ** 2
+        assert np.allclose(row, want, rtol=0, atol=1e-13 * want[n])

@@ -74,6 +74,7 @@ PINS = [
     TP.test_box_matrices_scale_and_keep_the_sparsity_on_any_box,
     TP.test_split_tiles_the_box_conformingly,
     TP.test_patch_tests_of_the_assembled_matrices,
+    TP.test_assembled_stiffness_is_the_seven_point_laplacian,
     lambda: TP.test_boundary_loads(3),
     TP.test_single_loaded_quad_shares,
     TP.test_transient_energy_balance_and_spectral_bound,

@@ -35,6 +35,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF*CG-iters/s"
+# What each precision computes in: "df64" is double-float arithmetic, a pair
+# of FP32 values with error-free sums and products (about 48 significant bits).
+DTYPE_DETAIL = {
+    "fp64": "FP64 vectors, operator and dot products",
+    "fp32_refined": ("inner CG in FP32 (vectors and operator; dot products summed in FP32 per warp, then FP64); "
+                     "outer refinement: FP64 solution, right-hand side and residual vectors with FP64 dot "
+                     "products, the residual's operator b - A x evaluated in double-float (df64, ~48 bits)"),
+    "fp32_plain": "FP32 vectors and operator; dot products summed in FP32 per warp, then FP64",
+}
 UNIT = "DOF*iter/s"
 WORKLOAD = "inclusions_cube_100: Q1 100^3 (1,030,301 DOF), 200 spherical inclusions k=10 rho_c=3, flux pulse z=1 for 50 steps, dt=1e-3, theta=0.5, 300 steps per forward solve, rtol 1e-10"
 FLUSH_BYTES = 256 << 20
@@ -750,7 +759,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32_refined": "f32+f64", "fp32_plain": "f32"}[args.precision],
+            "dtype": {"fp64": "f64", "fp32_refined": "f32+df64+f64", "fp32_plain": "f32"}[args.precision],
+            "dtype_detail": DTYPE_DETAIL[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision, "dof": nn,
                        "time_steps_per_forward_solve": args.nsteps, "cg_iterations_per_step_avg": its / (args.steps * args.nsteps),

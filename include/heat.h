@@ -384,13 +384,17 @@ heat_status heat_mh_stats(const heat_mh* mh, long long* solves, long long* cg_it
 
 /* ---- allocation-free operator call ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: code running during CUDA graph capture
- * (allocation cannot be captured), real-time loops that forbid allocation after
- * start-up, and hosts whose memory manager owns all device memory. It computes
- * y = A' x and *xdoty = x . A' x (A' as in heat_apply) on caller-owned device
- * buffers and allocates nothing: its reduction scratch (one partial sum per
- * tile of 32x4x8 nodes, and a counter) lives in a fixed 32 KiB device array
- * that every GPU loading the library holds until exit.
+ * that cannot allocate device memory: real-time loops that forbid allocation
+ * after start-up, and hosts whose memory manager owns all device memory and
+ * hands out only the buffers it was given. It computes y = A' x and
+ * *xdoty = x . A' x on caller-owned device buffers, where A' is the step
+ * matrix M/dt + theta K of trilinear boxes (heat_params.element = HEAT_ELEM_Q1
+ * only; this call has no six-tetrahedra form) with Dirichlet rows and columns
+ * replaced by the identity, as heat_apply computes it for such a simulation.
+ * It allocates nothing: its reduction scratch (one partial sum per tile of
+ * 32x4x8 nodes, and a counter) lives in a fixed file-scope device array of
+ * (HEAT_NOALLOC_MAX_TILES + 32) doubles = 33,024 bytes that every GPU loading
+ * the library holds until exit.
  *   nx, ny, nz, extent: the mesh, as in heat_create_mesh. At most
  *     HEAT_NOALLOC_MAX_TILES tiles, i.e. ceil((nx+1)/32)*ceil((ny+1)/4)*
  *     ceil((nz+1)/8) <= 4096 (for example 127^3 elements); larger meshes
@@ -398,12 +402,15 @@ heat_status heat_mh_stats(const heat_mh* mh, long long* solves, long long* cg_it
  *   dt, theta, dirichlet_faces: as in heat_params / heat_bc.
  *   coef: device, 2*Ne doubles, (rho_c, k) interleaved per element, element
  *     order, 16-byte aligned. x, y: device, N doubles. xdoty: device, 1 double.
+ *     The library cannot check device buffer sizes: buffers shorter than
+ *     these are read or written out of bounds.
  *   cuda_stream: stream of the launch (NULL: legacy default stream).
- * Calls share the scratch array and it keeps the last call's contents, so
- * calls that overlap on the GPU (other streams or host threads) race: the
- * caller must serialise them. The first call on each device looks up the
- * array's address with that device current; make it before any stream
- * capture. The call is asynchronous on cuda_stream. */
+ * Calls share the scratch array and it keeps the last call's contents (the
+ * call clears the counter it needs before its launch), so calls that overlap
+ * on the GPU (other streams or host threads) race: the caller must serialise
+ * them. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. The call is asynchronous on cuda_stream. */
 #define HEAT_NOALLOC_MAX_TILES 4096
 heat_status heat_apply_dot_noalloc(int nx, int ny, int nz, const double extent[3], double dt,
                                    double theta, uint32_t dirichlet_faces, const double* coef,

@@ -19,8 +19,11 @@ import scipy.sparse.linalg as spla
 
 
 def pcg(A, b: np.ndarray, x0: np.ndarray, pinv: np.ndarray, rtol: float,
-        max_iter: int = 20000, resid_period: int = 50):
-    """Algorithm 1. Returns (x, iterations, delta_final, delta_b)."""
+        max_iter: int = 20000, resid_period: int = 50, record: list = None):
+    """Algorithm 1. Returns (x, iterations, delta_final, delta_b).
+
+    With a list as `record`, each iteration appends its (alpha, beta), the
+    coefficients lanczos_extremes turns into a condition estimate."""
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - A @ x
     d = pinv * r
@@ -41,8 +44,30 @@ def pcg(A, b: np.ndarray, x0: np.ndarray, pinv: np.ndarray, rtol: float,
         delta_new = float(r @ s)
         beta = delta_new / delta_old
         d = s + beta * d
+        if record is not None:
+            record.append((alpha, beta))
         i += 1
     return x, i, delta_new, delta_b
+
+
+def lanczos_extremes(coeffs):
+    """Smallest and largest eigenvalue of the Lanczos tridiagonal matrix that a
+    preconditioned CG run builds implicitly (the CG-Lanczos relation, e.g. Saad,
+    Iterative Methods for Sparse Linear Systems, 2nd ed., §6.7.3): with the
+    run's (alpha_j, beta_j),
+        T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},   T_{j,j+1} = sqrt(beta_j)/alpha_j.
+    Its eigenvalues (Ritz values) approach the extreme eigenvalues of P^-1 A
+    from inside, so lam_max / lam_min estimates kappa(P^-1 A) from below."""
+    m = len(coeffs)
+    if m == 0:
+        return float("nan"), float("nan")
+    al = np.array([c[0] for c in coeffs])
+    be = np.array([c[1] for c in coeffs])
+    diag = 1.0 / al
+    diag[1:] += be[:-1] / al[:-1]
+    off = np.sqrt(be[:-1]) / al[:-1]
+    ev = sla.eigh_tridiagonal(diag, off, eigvals_only=True)
+    return float(ev[0]), float(ev[-1])
 
 
 def solve_direct(A, b: np.ndarray) -> np.ndarray:

@@ -473,8 +473,35 @@ def heat_destroy_batch(batch):
         _lib.heat_destroy_batch(batch)
 
 
+def _check_noalloc_args(nx, ny, nz, coef, x, y, xdoty):
+    """The C entry point cannot see device buffer sizes: check them here, with
+    dtype and device, before any pointer reaches it."""
+    nx, ny, nz = int(nx), int(ny), int(nz)
+    if nx < 1 or ny < 1 or nz < 1:
+        raise ValueError("heat_apply_dot_noalloc: mesh sizes must be >= 1")
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    need = {"coef": 2 * nx * ny * nz, "x": nn, "y": nn, "xdoty": 1}
+    tens = {"coef": coef, "x": x, "y": y, "xdoty": xdoty}
+    import torch
+    for name, t in tens.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"heat_apply_dot_noalloc: {name} must be a torch tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"heat_apply_dot_noalloc: {name} must be float64, got {t.dtype}")
+        if name == "xdoty" and t.numel() < 1 or name != "xdoty" and t.numel() != need[name]:
+            raise ValueError(f"heat_apply_dot_noalloc: {name} needs {need[name]} values, got {t.numel()}")
+    for name, t in tens.items():
+        if not t.is_cuda:
+            raise ValueError(f"heat_apply_dot_noalloc: {name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"heat_apply_dot_noalloc: {name} is on cuda:{t.device.index}, "
+                             f"the current device is cuda:{torch.cuda.current_device()}")
+
+
 def heat_apply_dot_noalloc(nx, ny, nz, extent, dt, theta, dirichlet_faces, coef, x, y, xdoty, stream=None):
-    """Allocation-free y = A' x and x.A'x on caller-owned CUDA tensors (see include/heat.h)."""
+    """Allocation-free y = A' x and x.A'x on caller-owned CUDA tensors (see include/heat.h).
+    Raises ValueError/TypeError for tensors of the wrong dtype, length or device."""
+    _check_noalloc_args(nx, ny, nz, coef, x, y, xdoty)
     load_library()
     ext = (C.c_double * 3)(*extent)
     s = C.c_void_p(int(stream) if stream else 0)

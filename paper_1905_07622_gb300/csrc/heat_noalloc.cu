@@ -1,18 +1,18 @@
 // heat_apply_dot_noalloc: the operator apply with its d.Ad dot product for
 // callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not capturable), real-time loops that forbid
-// allocation after start-up, and hosts whose memory manager owns all device
-// memory and hands out only the buffers it was given. Those callers already
-// hold their inputs and outputs; what they cannot provide is the kernel's
-// reduction scratch (one partial sum per tile plus a completion counter).
-// This entry point keeps that scratch in a fixed file-scope device array, so
-// a call allocates nothing: no cudaMalloc, no cudaFree, no allocating library
-// routine.
+// Some callers cannot call cudaMalloc: real-time loops that forbid allocation
+// after start-up, and hosts whose memory manager owns all device memory and
+// hands out only the buffers it was given. Those callers already hold their
+// inputs and outputs; what they cannot provide is the kernel's reduction
+// scratch (one partial sum per tile plus a completion counter). This entry
+// point keeps that scratch in a fixed file-scope device array, so a call
+// allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+// routine. It covers trilinear boxes only.
 //
 // Consequences for the caller:
-//   * every GPU that loads the library holds the array (32 KiB) until exit;
+//   * every GPU that loads the library holds the array, (4096 + 32) doubles =
+//     33,024 bytes, until exit;
 //   * every call shares it, and it keeps the last call's contents: calls that
 //     overlap on the GPU (two streams, or two host threads) race on it and
 //     must be serialised by the caller;

@@ -108,3 +108,29 @@ def test_tuning_table_host_logic(lib):
                                          "pw_quads": [1, 2, 4]}
     finally:
         api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
+
+
+@pytest.mark.parametrize("bad", ["f32_coef", "short_coef", "short_x", "long_y", "empty_dot", "cpu"])
+def test_noalloc_binding_rejects_bad_tensors_before_the_call(bad):
+    """heat_apply_dot_noalloc's binding checks dtype, length and device of every
+    buffer: the C entry point cannot, and a short device buffer would be read
+    or written out of bounds."""
+    torch = pytest.importorskip("torch")
+    import paper_1905_07622_gb300.api as api
+    nx, ny, nz = 3, 4, 5
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    f64 = dict(dtype=torch.float64)
+    t = {"coef": torch.zeros(2 * nx * ny * nz, **f64), "x": torch.zeros(nn, **f64),
+         "y": torch.zeros(nn, **f64), "xdoty": torch.zeros(1, **f64)}
+    if bad == "f32_coef":
+        t["coef"] = t["coef"].float()
+    elif bad == "short_coef":
+        t["coef"] = t["coef"][:-1]
+    elif bad == "short_x":
+        t["x"] = t["x"][:-2]
+    elif bad == "long_y":
+        t["y"] = torch.zeros(nn + 1, **f64)
+    elif bad == "empty_dot":
+        t["xdoty"] = torch.zeros(0, **f64)
+    with pytest.raises((ValueError, TypeError)):
+        api.heat_apply_dot_noalloc(nx, ny, nz, (1.0, 1.0, 1.0), 1e-3, 0.5, 0, t["coef"], t["x"], t["y"], t["xdoty"])

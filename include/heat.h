@@ -45,6 +45,7 @@ typedef struct heat_mesh heat_mesh;
 typedef struct heat_sim heat_sim;
 typedef struct heat_batch heat_batch;
 typedef struct heat_server heat_server;
+typedef struct heat_slab heat_slab;
 
 typedef enum {
   HEAT_OK = 0,
@@ -381,6 +382,64 @@ heat_status heat_mh_run(heat_mh* mh, int niter, double step, const double* norma
 /* Forward solves and CG iterations (all kinds, as heat_step_stats.iters) run
  * by the driver so far (either pointer may be NULL). */
 heat_status heat_mh_stats(const heat_mh* mh, long long* solves, long long* cg_iters);
+
+/* ---- one simulation split into z-slabs -------------------------------------
+ * The partitioned form of the dual-GPU split of §4.4 (Table 1 of §5.2 times
+ * it): the element layers of the mesh are cut into nslabs contiguous ranges
+ * along z and each slab keeps its own buffers for the node layers it owns plus
+ * one ghost node layer per neighbour. Every slab lives on the current GPU.
+ * Operator passes of a slab read only its own buffers; the kernels that write
+ * a slab's lowest or highest owned layer of a vector an operator pass reads
+ * (x, u = P^-1 r, Algorithm 1's d) store those values into the neighbour's
+ * ghost layer too (one node layer per interface and vector). Every CG scalar
+ * is summed per slab in tile order and then over slabs in slab order.
+ * FP64, trilinear boxes, Jacobi preconditioner. Two iteration forms:
+ *   merged = 1: the Chronopoulos-Gear form of CG, whose two inner products
+ *     (r.P^-1 r and (A u).u) come from one reduction per iteration.
+ *   merged = 0: Algorithm 1 (§3.3), two reductions per iteration (d.q and
+ *     r.P^-1 r).
+ * Both recompute r = b - A x every resid_period iterations, and when the
+ * recurrence residual meets the stopping rule; a step closes on that true
+ * residual only (as heat_step's FP64 path). The stopping rule,
+ * the right-hand side, the initial guess and the Dirichlet and flux handling
+ * are those of heat_step (§3.1, Algorithm 1).
+ *
+ * heat_slab_plan: the partition only (host, no GPU): first_layer[s] for
+ *   s = 0..nslabs is the first node layer slab s owns,
+ *   floor(s (nz + 1) / nslabs), and first_layer[nslabs] = nz + 1. Slab s owns
+ *   node layers [first_layer[s], first_layer[s+1]). Needs
+ *   1 <= nslabs <= min(nz + 1, 4096); else HEAT_ERR_ARG. */
+heat_status heat_slab_plan(int nz, int nslabs, int* first_layer);
+/* mesh, bc: as heat_sim_create. prm: precision HEAT_FP64, element
+ * HEAT_ELEM_Q1, cheb_degree < 2 (else HEAT_ERR_ARG); poll_period is the
+ * number of iterations queued between host polls. cuda_stream: the stream
+ * of every launch and copy (NULL: legacy default stream). The library owns
+ * every buffer; heat_slab_info reports their bytes. */
+heat_status heat_slab_create(const heat_mesh* mesh, const heat_bc* bc, const heat_params* prm, int nslabs,
+                             int merged, void* cuda_stream, heat_slab** out);
+/* Host arrays of Ne values each, element order: rho*C > 0 and k > 0, finite
+ * (else HEAT_ERR_ARG and nothing changes). Copies each slab's element layers
+ * (its owned ones and the layer below its first owned node layer) and
+ * derives P^-1, the Dirichlet lift and the face loads. Synchronous. */
+heat_status heat_slab_set_coeffs(heat_slab* slab, const double* rho_c, const double* k);
+/* Host array of N node values, node order: the state U^0 (Dirichlet nodes
+ * take their face values). Resets the step count. Synchronous. */
+heat_status heat_slab_set_state(heat_slab* slab, const double* u);
+/* Host array of N values: the current state, gathered from the owned layers
+ * of every slab. */
+heat_status heat_slab_get_state(heat_slab* slab, double* u);
+/* Advance nsteps time steps (the host polls the device phase every
+ * poll_period iterations). Errors as heat_step: HEAT_ERR_NOT_CONVERGED,
+ * HEAT_ERR_NONFINITE or HEAT_ERR_BREAKDOWN leave the state at the last
+ * completed step; stats (may be NULL) as heat_step_stats. */
+heat_status heat_slab_step(heat_slab* slab, int nsteps, heat_step_stats* stats);
+/* CG iterations of each step of the last heat_slab_step call (at most cap
+ * written to out, host; *n = the number logged). */
+heat_status heat_slab_step_iterations(heat_slab* slab, int* out, int cap, int* n);
+/* nslabs, the partition (nslabs + 1 ints, may be NULL) and the device bytes
+ * of the slabs' vectors and coefficients (may be NULL). */
+heat_status heat_slab_info(const heat_slab* slab, int* nslabs, int* first_layer, long long* device_bytes);
+void heat_destroy_slab(heat_slab* slab);
 
 /* ---- allocation-free operator call ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

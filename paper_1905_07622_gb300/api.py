@@ -158,6 +158,16 @@ _SIGS = [
     ("heat_mh_loglik", C.c_int, [_VP, _VP, _VP]),
     ("heat_mh_run", C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("heat_mh_stats", C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    ("heat_slab_plan", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    ("heat_slab_create", C.c_int, [_VP, C.POINTER(heat_bc), C.POINTER(heat_params), C.c_int, C.c_int, _VP,
+                                   C.POINTER(_VP)]),
+    ("heat_slab_set_coeffs", C.c_int, [_VP, _VP, _VP]),
+    ("heat_slab_set_state", C.c_int, [_VP, _VP]),
+    ("heat_slab_get_state", C.c_int, [_VP, _VP]),
+    ("heat_slab_step", C.c_int, [_VP, C.c_int, C.POINTER(heat_step_stats)]),
+    ("heat_slab_step_iterations", C.c_int, [_VP, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
+    ("heat_slab_info", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    ("heat_destroy_slab", None, [_VP]),
     ("heat_checks_compiled", C.c_int, []),
     ("heat_check_violations", C.c_int, [_VP, C.POINTER(C.c_uint)]),
     ("heat_last_error", C.c_char_p, []),
@@ -758,3 +768,124 @@ class Simulation:
 
 
 load_library()
+
+
+# ---- one simulation split into z-slabs (include/heat.h, §4.4) -------------
+
+def heat_slab_plan(nz: int, nslabs: int) -> list:
+    """First owned node layer of each slab, plus nz + 1 (host only, no GPU)."""
+    load_library()
+    out = (C.c_int * (int(nslabs) + 1))()
+    _check(_lib.heat_slab_plan(int(nz), int(nslabs), out))
+    return list(out)
+
+
+def heat_slab_create(mesh, bc, prm, nslabs: int, merged: bool = True, stream=None):
+    load_library()
+    out = _VP()
+    s = C.c_void_p(int(stream) if stream else 0)
+    _check(_lib.heat_slab_create(mesh, C.byref(bc), C.byref(prm), int(nslabs), 1 if merged else 0, s,
+                                 C.byref(out)))
+    return out
+
+
+def heat_slab_set_coeffs(slab, rho_c, k, ne: int):
+    a, b = _host_f64(rho_c, ne), _host_f64(k, ne)
+    _check(_lib.heat_slab_set_coeffs(slab, a.ctypes.data, b.ctypes.data))
+
+
+def heat_slab_set_state(slab, u, nn: int):
+    a = _host_f64(u, nn)
+    _check(_lib.heat_slab_set_state(slab, a.ctypes.data))
+
+
+def heat_slab_get_state(slab, nn: int) -> np.ndarray:
+    out = np.empty(nn)
+    _check(_lib.heat_slab_get_state(slab, out.ctypes.data))
+    return out
+
+
+def heat_slab_step(slab, nsteps: int) -> dict:
+    """Advance nsteps; returns heat_step_stats as a dict (raises HeatError on failure)."""
+    st = heat_step_stats()
+    rc = _lib.heat_slab_step(slab, int(nsteps), C.byref(st))
+    d = st.as_dict()
+    if rc != HEAT_OK:
+        raise HeatError(rc, _lib.heat_last_error().decode())
+    return d
+
+
+def heat_slab_step_iterations(slab, cap: int = 1 << 16) -> list:
+    out = (C.c_int * cap)()
+    n = C.c_int()
+    _check(_lib.heat_slab_step_iterations(slab, out, cap, C.byref(n)))
+    return list(out[: min(cap, n.value)])
+
+
+def heat_slab_info(slab) -> dict:
+    ns = C.c_int()
+    _check(_lib.heat_slab_info(slab, C.byref(ns), None, None))
+    first = (C.c_int * (ns.value + 1))()
+    nb = C.c_longlong()
+    _check(_lib.heat_slab_info(slab, C.byref(ns), first, C.byref(nb)))
+    return {"nslabs": ns.value, "first_layer": list(first), "device_bytes": nb.value}
+
+
+def heat_destroy_slab(slab):
+    if slab:
+        _lib.heat_destroy_slab(slab)
+
+
+class SlabSimulation:
+    """One Problem split into z-slabs on the current GPU (heat_slab_*)."""
+
+    def __init__(self, mesh, slab, nn, ne):
+        self.mesh, self.slab, self.nn, self.ne = mesh, slab, nn, ne
+
+    @classmethod
+    def from_problem(cls, p, nslabs: int, merged: bool = True, stream=None, **param_overrides):
+        mesh = heat_create_mesh(p.nx, p.ny, p.nz, p.origin, p.extent)
+        try:
+            nn, ne = heat_mesh_sizes(mesh)
+            kw = dict(theta=p.theta, dt=p.dt, rtol=p.rtol, precision="fp64")
+            kw.update(param_overrides)
+            prm = heat_params_default(**kw)
+            bc = make_bc(p.dirichlet, p.flux, p.flux_steps)
+            slab = heat_slab_create(mesh, bc, prm, nslabs, merged, stream)
+        except Exception:
+            heat_destroy_mesh(mesh)
+            raise
+        self = cls(mesh, slab, nn, ne)
+        try:
+            heat_slab_set_coeffs(slab, p.rho_c, p.k, ne)
+            heat_slab_set_state(slab, p.u0, nn)
+        except Exception:
+            self.close()
+            raise
+        return self
+
+    def step(self, nsteps):
+        return heat_slab_step(self.slab, nsteps)
+
+    def state(self) -> np.ndarray:
+        return heat_slab_get_state(self.slab, self.nn)
+
+    def set_state(self, u):
+        heat_slab_set_state(self.slab, u, self.nn)
+
+    def iterations(self) -> list:
+        return heat_slab_step_iterations(self.slab)
+
+    def close(self):
+        if self.slab:
+            heat_destroy_slab(self.slab)
+            self.slab = None
+        if self.mesh:
+            heat_destroy_mesh(self.mesh)
+            self.mesh = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

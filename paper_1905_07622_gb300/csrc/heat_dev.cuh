@@ -59,7 +59,7 @@ struct SimScalars {
   int cgs;             // FP32 fused iteration: current slot of r, w, s (0/1)
   int y_valid;         // bit v: yv[v] holds A' vec64[v] (FP32 paths, see k_open)
   int cheb_k;          // next Chebyshev pass (1 .. cheb_m - 1) while phase is PH_CHEB
-  int pad_sc_;
+  int confirm;         // FP64 path: the running PH_RESID pass confirms convergence (not an iteration)
   unsigned int check_violations;  // out-of-range indices met (HEAT_CHECK builds)
   double delta;    // r^T P^-1 r of the current solve
   double delta_b;  // b^T P^-1 b of the step

@@ -21,11 +21,11 @@ quantity the stopping test saw) and in the oracle (the quantity checked here):
 of the arithmetic that formed the tested residual and c the number of rounded
 operations one output of the operator passes through, at most 64 on both
 sides (27 terms, or the factorised form's three butterfly levels each way, its
-scaling and the face and node sums). The FP64 path tests its recurrence
-residual, which drifts from the true one by at most one such rounding term
-per iteration since the last replacement (at most resid_period = 50 of them).
-The refined path tests its true residual formed in double-float arithmetic
-(u = 2^-48). A defect in the operator, a boundary or the schedule gives
+scaling and the face and node sums). Both paths close a step on a true
+residual b - A x: the FP64 path recomputes it in FP64 once its recurrence
+residual meets the rule (the recurrence drifts from b - A x by far more than
+rounding on the 200^3 layered cube, 1.9e-10 against 1e-10), and the refined
+path forms it in double-float arithmetic (u = 2^-48). A defect in the operator, a boundary or the schedule gives
 rho of the order of 1 against bounds of 1e-10 to 1e-8.
 """
 import numpy as np
@@ -42,9 +42,10 @@ C_OPS = 64
 
 
 def rounding_unit(precision):
-    """Unit roundoff times operations of the residual the stopping test saw."""
+    """Unit roundoff times operations: the GPU's evaluation of the residual
+    its stopping test saw, plus the oracle's evaluation here (FP64)."""
     if precision == "fp64":
-        return (50 + 1) * C_OPS * U64
+        return 2 * C_OPS * U64
     return C_OPS * UDF + C_OPS * U64
 
 

@@ -83,6 +83,9 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   int w_items;                // work items (groups of segment tiles per block)
   int fused;                  // the engine runs the FP32 inner solve as one fused kernel per iteration
   int w_pad_;
+  // warp-segment tiles of the step-start and refinement passes (k_open_w):
+  // (SX-2) x NY x o_tz nodes each, o_items work items
+  int o_ntx, o_nty, o_ntz, o_tz, o_ntiles, o_items;
   long long nn;               // nodes
   uint32_t dir_faces;         // Dirichlet face bits
   int prec;                   // Prec

@@ -45,6 +45,16 @@ template <> struct Pair2<double> {
   }
 };
 
+// Double-float pairs (df.cuh): the refinement passes' arithmetic, about 48
+// significant bits from FP32 instructions.
+template <> struct Pair2<DF> {
+  using t = DF2;
+  static __device__ __forceinline__ DF2 make(DF a, DF b) { return DF2{a, b}; }
+  static __device__ __forceinline__ DF2 add(DF2 a, DF2 b) { return DF2{a.x + b.x, a.y + b.y}; }
+  static __device__ __forceinline__ DF2 mul(DF2 a, DF2 b) { return DF2{a.x * b.x, a.y * b.y}; }
+  static __device__ __forceinline__ DF2 fma(DF2 a, DF2 b, DF2 c) { return DF2{a.x * b.x + c.x, a.y * b.y + c.y}; }
+};
+
 // Geometry of one lane of a segment tile: which of its rows exist, which are
 // Dirichlet, where its column starts.
 template <int NY>
@@ -126,8 +136,8 @@ struct RegSrc {
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
       Coef z;
-      z.x = T(0);
-      z.y = T(0);
+      z.x = 0;
+      z.y = 0;
       const int e = lg.ebase + r * lg.enx + E * lg.estride;
       cf[r] = (((le >> r) & 1u) && HEAT_INDEX_OK(lg.sc, e, lg.ne)) ? coef[e] : z;
     }

@@ -11,7 +11,9 @@ the step equation of §3.1 on the free rows,
 element-by-element product the oracle forms over the whole mesh
 (fem.apply_all). The solver's stopping rule (Algorithm 1 with the relative
 reading) ends a step when r^T P^-1 r <= rtol^2 b^T P^-1 b, P the Jacobi
-diagonal and b the right-hand side above. So in the P^-1-weighted norm
+diagonal and b the right-hand side of the eliminated system on the free rows,
+b = (L u^{n-1} + F^n) - A_{fD} g: the Dirichlet columns of A move to the
+right-hand side. So in the P^-1-weighted norm
 
     rho = ||r||_{P^-1} / ||b||_{P^-1}  <=  rtol + c * u * ||A||u^n|| ||_{P^-1} / ||b||_{P^-1},
 
@@ -23,9 +25,8 @@ operations one output of the operator passes through, at most 64 on both
 sides (27 terms, or the factorised form's three butterfly levels each way, its
 scaling and the face and node sums). Both paths close a step on a true
 residual b - A x: the FP64 path recomputes it in FP64 once its recurrence
-residual meets the rule (the recurrence drifts from b - A x by far more than
-rounding on the 200^3 layered cube, 1.9e-10 against 1e-10), and the refined
-path forms it in double-float arithmetic (u = 2^-48). A defect in the operator, a boundary or the schedule gives
+residual meets the rule, and the refined path forms it in double-float
+arithmetic (u = 2^-48). A defect in the operator, a boundary or the schedule gives
 rho of the order of 1 against bounds of 1e-10 to 1e-8.
 """
 import numpy as np
@@ -56,13 +57,19 @@ def step_residual(p, u_prev, u_new, n):
     if p.flux and transient.flux_on(p, n):
         b += fem.flux_vector(p)
     au = fem.apply_all(p, u_new, 1.0 / p.dt, p.theta, eliminate=False)
+    dn = fem.dirichlet_nodes(p)[0]
+    g = np.zeros(p.n_nodes)
+    g[dn] = u_new[dn]
+    lift = fem.apply_all(p, g, 1.0 / p.dt, p.theta, eliminate=False)  # A_{.D} g
+    # r = A_ff u_f - b_f with b_f = b - A_fD g on the free rows: au - b as before
+    b = b - lift
     absau = fem.apply_all(p, u_new, 1.0 / p.dt, p.theta, eliminate=False, absolute=True)
     d = fem.diagonal_all(p, 1.0 / p.dt, p.theta)
     free = np.ones(p.n_nodes, dtype=bool)
-    free[fem.dirichlet_nodes(p)[0]] = False
+    free[dn] = False
     w = 1.0 / d[free]
     nb = np.sqrt(np.sum(b[free] ** 2 * w))
-    rho = np.sqrt(np.sum((au - b)[free] ** 2 * w)) / nb
+    rho = np.sqrt(np.sum((au - lift - b)[free] ** 2 * w)) / nb
     scale = np.sqrt(np.sum(absau[free] ** 2 * w)) / nb
     return rho, scale
 

@@ -510,11 +510,17 @@ heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flus
  *   seg_nodes[b]: output nodes per warp-segment tile for meshes of bucket b
  *     (N < 200000, N < 4000000, larger); 32 .. 2^20, default 512.
  *   pw_quads[p]: for heat_precision p, groups of 4 nodes each thread of the
- *     pointwise update kernel handles (1, 2 or 4; default {2, 4, 4}). */
+ *     pointwise update kernel handles (1, 2 or 4; default {2, 4, 4}).
+ *   open_w[p]: for heat_precision p, 1 runs the step-start and refinement
+ *     residual passes (§3.1's right-hand side, the true residual of
+ *     Algorithm 1 and of the refinement) in the warp-segment march with
+ *     two-row segments, 0 in block tiles (default {0, 0, 0}; trilinear boxes
+ *     only, six-tetrahedra boxes always use block tiles). */
 typedef struct heat_tuning {
   int variant[3];
   int seg_nodes[3];
   int pw_quads[3];
+  int open_w[3];
 } heat_tuning;
 int heat_tuning_num_variants(void);
 /* Shape of variant v: segment width in nodes along x (one lane per node),

@@ -85,10 +85,12 @@ class heat_mh_config(C.Structure):
 
 
 class heat_tuning(C.Structure):
-    _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3), ("pw_quads", C.c_int * 3)]
+    _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3), ("pw_quads", C.c_int * 3),
+                ("open_w", C.c_int * 3)]
 
     def as_dict(self):
-        return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes), "pw_quads": list(self.pw_quads)}
+        return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes), "pw_quads": list(self.pw_quads),
+                "open_w": list(self.open_w)}
 
 
 class heat_server_stats(C.Structure):
@@ -550,12 +552,17 @@ def heat_tuning_get() -> dict:
     return t.as_dict()
 
 
-def heat_tuning_set(variant, seg_nodes, pw_quads=None):
-    """Set the table; pw_quads=None keeps the current pointwise item sizes."""
+def heat_tuning_set(variant, seg_nodes, pw_quads=None, open_w=None):
+    """Set the table; pw_quads=None / open_w=None keep the current pointwise
+    item sizes / open-pass forms."""
     load_library()
+    cur = heat_tuning_get()
     if pw_quads is None:
-        pw_quads = heat_tuning_get()["pw_quads"]
-    t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes), (C.c_int * 3)(*pw_quads))
+        pw_quads = cur["pw_quads"]
+    if open_w is None:
+        open_w = cur["open_w"]
+    t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes), (C.c_int * 3)(*pw_quads),
+                    (C.c_int * 3)(*open_w))
     _check(_lib.heat_tuning_set(C.byref(t)))
 
 

@@ -34,7 +34,23 @@ struct KernelSet {
   // Chebyshev passes: block form, and the warp form matching apply_w (which
   // then replaces it, on the same work list)
   TileFn cheb, cheb_w;
+  // step-start and refinement passes in the warp-segment march (replaces
+  // `open` when set), on their own segment geometry and work list
+  TileFn open_w = nullptr;
+  int owsx = 0, owny = 0, owwarps = 0;
 };
+
+// The warp-segment form of k_open for precision prec: 32-lane segments of 2
+// rows, 4 warps per block (double-float on the FP32 paths, FP64 on the FP64
+// path; the two-row segment keeps the double-width values in registers).
+constexpr int kOpenSX = 32, kOpenNY = 2, kOpenWarps = 4;
+static TileFn open_w_kernel(int prec) {
+  switch (prec) {
+    case P_FP64: return k_open_w<P_FP64, kOpenSX, kOpenNY, kOpenWarps, 1>;
+    case P_FP32_REFINED: return k_open_w<P_FP32_REFINED, kOpenSX, kOpenNY, kOpenWarps, 2>;
+    default: return k_open_w<P_FP32_PLAIN, kOpenSX, kOpenNY, kOpenWarps, 2>;
+  }
+}
 
 template <int P, int SX, int SY, int E = E_Q1>
 static KernelSet make_set() {
@@ -108,7 +124,7 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // variant per precision (-1: the block-tile apply) and the segment tile size
 // per mesh-size bucket. Both are fixed per simulation size, so results stay
 // bitwise identical alone and in batches built under the same table.
-static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}};
+static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}, {0, 0, 0}};
 static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }
@@ -140,6 +156,9 @@ heat_status tuning_set(const Tuning& t) {
   for (int p = 0; p < 3; ++p)
     if (t.pw_quads[p] != 1 && t.pw_quads[p] != 2 && t.pw_quads[p] != 4)
       return set_error(HEAT_ERR_ARG, "tuning: pointwise groups %d not 1, 2 or 4", t.pw_quads[p]);
+  for (int p = 0; p < 3; ++p)
+    if (t.open_w[p] != 0 && t.open_w[p] != 1)
+      return set_error(HEAT_ERR_ARG, "tuning: open_w[%d] = %d not 0 or 1", p, t.open_w[p]);
   for (int b = 0; b < 3; ++b)
     if (t.seg_nodes[b] < 32 || t.seg_nodes[b] > (1 << 20))
       return set_error(HEAT_ERR_ARG, "tuning: segment size %d out of range", t.seg_nodes[b]);
@@ -198,6 +217,12 @@ static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int el
         cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
     }
   }
+  if (elem == E_Q1 && t.open_w[prec]) {
+    k.open_w = open_w_kernel(prec);
+    k.owsx = kOpenSX;
+    k.owny = kOpenNY;
+    k.owwarps = kOpenWarps;
+  }
   for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
   const int qpt = t.pw_quads[prec];
   k.pw_chunk = pw_chunk(qpt);
@@ -235,7 +260,12 @@ struct Engine {
   long long cap_aw = 0;
   int grid_aw = 0;
   std::vector<int2> h_aw;
-  int* d_nwork = nullptr;  // [0] operator tiles, [1] pointwise chunks, [2] warp-apply items
+  int2* d_work_ow = nullptr;  // warp-segment open-pass items
+  long long cap_ow = 0;
+  int grid_ow = 0;
+  std::vector<int2> h_ow;
+  // [0] operator tiles, [1] pointwise chunks, [2] warp-apply items, [3] warp open-pass items
+  int* d_nwork = nullptr;
   int* d_unfinished = nullptr;
   int* h_unfinished = nullptr;
   double* d_partial = nullptr;
@@ -299,6 +329,19 @@ static void tile_geometry(SimDev& d, const KernelSet& ks) {
     const int spc = ks.wwarps * (32 / ks.wsx);
     d.w_items = (d.w_ntiles + spc - 1) / spc;
   }
+  d.o_ntx = d.o_nty = d.o_ntz = d.o_tz = d.o_ntiles = d.o_items = 0;
+  if (ks.open_w) {
+    // about kOpenSegNodes output nodes per segment tile, at least 4 levels
+    constexpr int kOpenSegNodes = 1024;
+    d.o_ntx = (d.nx + 1 + ks.owsx - 3) / (ks.owsx - 2);
+    d.o_nty = (d.ny + 1 + ks.owny - 1) / ks.owny;
+    const int tz0 = std::max(4, std::min(levels, kOpenSegNodes / ((ks.owsx - 2) * ks.owny)));
+    d.o_ntz = (levels + tz0 - 1) / tz0;
+    d.o_tz = (levels + d.o_ntz - 1) / d.o_ntz;
+    d.o_ntiles = d.o_ntx * d.o_nty * d.o_ntz;
+    const int spc = ks.owwarps * (32 / ks.owsx);
+    d.o_items = (d.o_ntiles + spc - 1) / spc;
+  }
 }
 
 static int sm_count() {
@@ -313,6 +356,7 @@ static heat_status engine_upload(Engine* e) {
   e->h_op.clear();
   e->h_pw.clear();
   e->h_aw.clear();
+  e->h_ow.clear();
   const int sms = sm_count();
   long long item_base = 0;
   for (size_t i = 0; i < e->sims.size(); ++i) {
@@ -320,16 +364,18 @@ static heat_status engine_upload(Engine* e) {
     tile_geometry(d, e->ks);
     d.fused = e->ks.fused ? 1 : 0;
     d.partial = e->d_partial + 4 * item_base;
-    item_base += std::max(std::max(d.ntiles, d.npw), d.w_items);
+    item_base += std::max(std::max(std::max(d.ntiles, d.npw), d.w_items), d.o_items);
     for (int t = 0; t < d.ntiles; ++t) e->h_op.push_back(make_int2((int)i, t));
     for (int t = 0; t < d.npw; ++t) e->h_pw.push_back(make_int2((int)i, t));
     for (int t = 0; t < d.w_items; ++t) e->h_aw.push_back(make_int2((int)i, t));
+    for (int t = 0; t < d.o_items; ++t) e->h_ow.push_back(make_int2((int)i, t));
     e->h_sims.push_back(d);
   }
   if ((long long)e->h_op.size() > e->cap_op || (long long)e->h_pw.size() > e->cap_pw ||
-      (long long)e->h_aw.size() > e->cap_aw || item_base > e->cap_partial)
+      (long long)e->h_aw.size() > e->cap_aw || (long long)e->h_ow.size() > e->cap_ow ||
+      item_base > e->cap_partial)
     return set_error(HEAT_ERR_ARG, "engine: work lists exceed their capacity");
-  const int nwork[3] = {(int)e->h_op.size(), (int)e->h_pw.size(), (int)e->h_aw.size()};
+  const int nwork[4] = {(int)e->h_op.size(), (int)e->h_pw.size(), (int)e->h_aw.size(), (int)e->h_ow.size()};
   CUDA_TRY(cudaMemcpyAsync(e->d_sims, e->h_sims.data(), sizeof(SimDev) * e->h_sims.size(), cudaMemcpyHostToDevice,
                            e->stream));
   CUDA_TRY(cudaMemcpyAsync(e->d_work_op, e->h_op.data(), sizeof(int2) * e->h_op.size(), cudaMemcpyHostToDevice,
@@ -338,6 +384,9 @@ static heat_status engine_upload(Engine* e) {
                            e->stream));
   if (!e->h_aw.empty())
     CUDA_TRY(cudaMemcpyAsync(e->d_work_aw, e->h_aw.data(), sizeof(int2) * e->h_aw.size(), cudaMemcpyHostToDevice,
+                             e->stream));
+  if (!e->h_ow.empty())
+    CUDA_TRY(cudaMemcpyAsync(e->d_work_ow, e->h_ow.data(), sizeof(int2) * e->h_ow.size(), cudaMemcpyHostToDevice,
                              e->stream));
   CUDA_TRY(cudaMemcpyAsync(e->d_nwork, nwork, sizeof(nwork), cudaMemcpyHostToDevice, e->stream));
   CUDA_TRY(cudaStreamSynchronize(e->stream));
@@ -351,6 +400,10 @@ static heat_status engine_upload(Engine* e) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ch, e->ks.cheb_w, 32 * e->ks.wwarps, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ch, e->ks.cheb, e->ks.apply_threads, 0);
+  int occ_ow = 1;
+  if (e->ks.open_w)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ow, e->ks.open_w, 32 * e->ks.owwarps, 0);
+  e->grid_ow = (int)std::max(1LL, std::min<long long>(nwork[3], (long long)sms * std::max(1, occ_ow)));
   e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
   e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
   e->grid_aw = (int)std::max(1LL, std::min<long long>(nwork[2], (long long)sms * std::max(1, occ_aw)));
@@ -415,7 +468,9 @@ static heat_status engine_capture(Engine* e) {
   apply_launch(e, &afn, &agrid, &athreads, &awork, &anwork, &asmem);
   cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
-    cudaError_t lerr = launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
+    cudaError_t lerr = e->ks.open_w
+                           ? launch(e->ks.open_w, e->grid_ow, 32 * e->ks.owwarps, e->d_work_ow, e->d_nwork + 3, 0)
+                           : launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
     for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
       for (int k = 0; k < e->ncheb && lerr == cudaSuccess; ++k) {
         if (e->ks.cheb_w) lerr = launch(e->ks.cheb_w, e->grid_ch, 32 * e->ks.wwarps, e->d_work_aw, e->d_nwork + 2, 0);
@@ -455,22 +510,24 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   e->ks = kernel_set(precision, tun ? *tun : tuning_get(), e->ncheb > 0, e->elem);
   e->stream = stream;
   // capacities: the geometry is a function of each mesh, so compute it
-  long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_partial = 0;
+  long long cap_op = 0, cap_pw = 0, cap_aw = 0, cap_ow = 0, cap_partial = 0;
   for (heat_sim* s : e->sims) {
     SimDev d = s->dev;
     tile_geometry(d, e->ks);
     cap_op += d.ntiles;
     cap_pw += d.npw;
     cap_aw += d.w_items;
-    cap_partial += std::max(std::max(d.ntiles, d.npw), d.w_items);
+    cap_ow += d.o_items;
+    cap_partial += std::max(std::max(std::max(d.ntiles, d.npw), d.w_items), d.o_items);
   }
-  if (cap_op > (1LL << 30) || cap_pw > (1LL << 30) || cap_aw > (1LL << 30)) {
+  if (cap_op > (1LL << 30) || cap_pw > (1LL << 30) || cap_aw > (1LL << 30) || cap_ow > (1LL << 30)) {
     delete e;
     return set_error(HEAT_ERR_ARG, "engine: too many work items");
   }
   e->cap_op = cap_op;
   e->cap_pw = cap_pw;
   e->cap_aw = cap_aw;
+  e->cap_ow = cap_ow;
   e->cap_partial = cap_partial;
   heat_status st = HEAT_OK;
   auto fail = [&](heat_status s) {
@@ -481,7 +538,8 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
       cudaMalloc(&e->d_work_op, sizeof(int2) * cap_op) != cudaSuccess ||
       cudaMalloc(&e->d_work_pw, sizeof(int2) * cap_pw) != cudaSuccess ||
       cudaMalloc(&e->d_work_aw, sizeof(int2) * std::max(1LL, cap_aw)) != cudaSuccess ||
-      cudaMalloc(&e->d_nwork, sizeof(int) * 3) != cudaSuccess ||
+      cudaMalloc(&e->d_work_ow, sizeof(int2) * std::max(1LL, cap_ow)) != cudaSuccess ||
+      cudaMalloc(&e->d_nwork, sizeof(int) * 4) != cudaSuccess ||
       cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_partial, sizeof(double) * 4 * cap_partial) != cudaSuccess ||
       cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess) {
@@ -513,6 +571,7 @@ void engine_destroy(Engine* e) {
   cudaFree(e->d_work_op);
   cudaFree(e->d_work_pw);
   cudaFree(e->d_work_aw);
+  cudaFree(e->d_work_ow);
   cudaFree(e->d_nwork);
   cudaFree(e->d_unfinished);
   cudaFree(e->d_partial);
@@ -653,7 +712,7 @@ long long engine_launches(const Engine* e) { return e->launches; }
 size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) {
   // the largest work lists any precision's kernels need under the current table
   const Tuning t = tuning_get();
-  long long op = 0, pw = 0, aw = 0;
+  long long op = 0, pw = 0, aw = 0, ow = 0;
   for (int p = 0; p < 3; ++p) {
     SimDev d{};
     d.nx = (int)nx;
@@ -664,9 +723,10 @@ size_t engine_footprint(long long nn, long long nx, long long ny, long long nz) 
     op = std::max<long long>(op, d.ntiles);
     pw = std::max<long long>(pw, d.npw);
     aw = std::max<long long>(aw, d.w_items);
+    ow = std::max<long long>(ow, d.o_items);
   }
-  return (size_t)(sizeof(int2) * (op + pw + aw) + sizeof(double) * 4 * std::max(std::max(op, pw), aw) +
-                  sizeof(SimDev) + 64);
+  return (size_t)(sizeof(int2) * (op + pw + aw + ow) +
+                  sizeof(double) * 4 * std::max(std::max(std::max(op, pw), aw), ow) + sizeof(SimDev) + 64);
 }
 
 // Reads a buffer larger than L2 so the next kernel starts cold. Reading (not

@@ -70,6 +70,7 @@ struct Tuning {
   int variant[3];
   int seg_nodes[3];
   int pw_quads[3];  // k_update: groups of 4 nodes per thread (1, 2 or 4), per precision
+  int open_w[3];    // per precision: 1 runs k_open's passes in the warp-segment march (k_open_w)
 };
 int size_bucket(long long nn);
 int num_variants();

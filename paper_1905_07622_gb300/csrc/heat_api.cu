@@ -845,6 +845,7 @@ extern "C" heat_status heat_tuning_get(heat_tuning* t) {
     t->variant[i] = x.variant[i];
     t->seg_nodes[i] = x.seg_nodes[i];
     t->pw_quads[i] = x.pw_quads[i];
+    t->open_w[i] = x.open_w[i];
   }
   return HEAT_OK;
 }
@@ -856,6 +857,7 @@ extern "C" heat_status heat_tuning_set(const heat_tuning* t) {
     x.variant[i] = t->variant[i];
     x.seg_nodes[i] = t->seg_nodes[i];
     x.pw_quads[i] = t->pw_quads[i];
+    x.open_w[i] = t->open_w[i];
   }
   return tuning_set(x);
 }

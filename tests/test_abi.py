@@ -86,11 +86,12 @@ def test_tuning_table_host_logic(lib):
     with pytest.raises(api.HeatError):
         api.heat_tuning_variant(n)
     old = api.heat_tuning_get()
-    assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512], "pw_quads": [2, 4, 4]}
+    assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512], "pw_quads": [2, 4, 4],
+                   "open_w": [0, 0, 0]}
     try:
-        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4])
+        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4], [1, 0, 1])
         assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
-                                         "pw_quads": [1, 2, 4]}
+                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1]}
         no64 = [v for v in range(n) if not shapes[v]["has_fp64"]]
         bad = [([-1, n, 0], [512] * 3), ([-2, 0, 0], [512] * 3), ([-1, 0, 0], [16, 512, 512]),
                ([-1, 0, 0], [512, 512, (1 << 20) + 1])]
@@ -103,11 +104,14 @@ def test_tuning_table_host_logic(lib):
         for quads in ([3, 4, 4], [2, 0, 4], [2, 4, 8]):
             with pytest.raises(api.HeatError):
                 api.heat_tuning_set([-1, 0, 0], [512] * 3, quads)
+        for ow in ([2, 1, 1], [0, -1, 1]):
+            with pytest.raises(api.HeatError):
+                api.heat_tuning_set([-1, 0, 0], [512] * 3, [2, 4, 4], ow)
         # a rejected table leaves the last good one in place
         assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
-                                         "pw_quads": [1, 2, 4]}
+                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1]}
     finally:
-        api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
+        api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"])
 
 
 @pytest.mark.parametrize("bad", ["f32_coef", "short_coef", "short_x", "long_y", "empty_dot", "cpu"])

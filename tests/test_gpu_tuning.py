@@ -180,3 +180,32 @@ def test_batch_autotune_rebuilds_and_keeps_parity():
     for g, p in zip(got, ps):
         ref = pins.oracle_steps(p)
         assert np.linalg.norm(g - ref.u[2]) <= 1e-8 * np.linalg.norm(ref.u[2])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_warp_segment_open_passes_match_block_tiles_and_oracle(precision):
+    """The step-start and refinement passes in the warp-segment march
+    (tuning open_w = 1) give the block-tile passes' fields and the oracle's."""
+    import paper_1905_07622_gb300 as hg
+    from oracle import transient
+    p = W.random_box(37, 9, 14, seed=19, dirichlet={4: 1.0, 1: -0.5}, flux={5: 1.0}, theta=0.5, dt=0.01,
+                     nsteps=4, flux_steps=2, rtol=1e-12, contrast=(0.1, 10.0))
+    ref = transient.run(p, solver="direct")
+    old = hg.heat_tuning_get()
+    fields = {}
+    try:
+        for ow in (0, 1):
+            hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], [ow, ow, ow])
+            with hg.Simulation.from_problem(p, precision=precision) as s:
+                us = []
+                for _ in range(p.nsteps):
+                    assert s.step(1)["status"] == 0
+                    us.append(s.state())
+            fields[ow] = us
+    finally:
+        hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"])
+    tol = 1e-9 if precision == "fp64" else 1e-8
+    for n in range(p.nsteps):
+        a, b = fields[0][n], fields[1][n]
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a), n
+        assert np.linalg.norm(b - ref.u[n + 1]) <= tol * np.linalg.norm(ref.u[n + 1]), n

@@ -75,9 +75,17 @@ def parse():
     ap.add_argument("--mh-chains", type=int, default=32,
                     help="corrosion inverse problem: Metropolis-Hastings chains solved as one batch (0: skip)")
     ap.add_argument("--mh-iters", type=int, default=8)
-    ap.add_argument("--serve-requests", type=int, default=40, help="serving stream length (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="serving stream at the configured rate: requests (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-low-requests", type=int, default=100,
+                    help="second serving stream at a rate one GPU sustains: requests (0: skip)")
+    ap.add_argument("--serve-low-rate", type=float, default=4.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--slab-steps", type=int, default=5,
+                    help="z-slab split of the 100^3 FP64 solve: time steps per slab count (0: skip)")
+    ap.add_argument("--slab-only", action="store_true", help="run only the z-slab leg")
+    ap.add_argument("--serve-only", action="store_true", help="run only the two serving streams")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning table")
     ap.add_argument("--tuning-json", default="",
                     help='set the kernel tuning table instead of autotuning, e.g. '
@@ -195,6 +203,32 @@ class ClockSampler:
 
 def cheb_degrees(args):
     return tuple(int(x) for x in args.cheb_degrees.split(",") if x.strip())
+
+
+# Algorithmic floating-point operations per node of the FP64 apply (the
+# factorised operator of the block tile and of the warp march): forward x 2,
+# forward y 4, per element (one per node) 4 x 13 for the two z-Walsh halves
+# (A, B, G, Tn), inverse y 4, node sums 5 = 67; the direction update
+# d = P^-1 r + beta d_old 3 and the dot product d.q 2. An FMA counts 2.
+FP64_APPLY_FLOPS_PER_NODE = 72
+_FP64_PEAK = None
+
+
+def fp64_peak_tflops(hg):
+    """The FP64 FMA rate of this GPU, measured once per run (heat_probe_fma_rate)."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        _FP64_PEAK = hg.heat_probe_fma_rate(True, 5)
+    return _FP64_PEAK
+
+
+def fp64_roofline(hg, nodes: int, ms_apply: float) -> dict:
+    """The FP64 apply against the measured FP64 FMA peak (its bound on this GPU)."""
+    peak = fp64_peak_tflops(hg)
+    achieved = FP64_APPLY_FLOPS_PER_NODE * nodes / (ms_apply * 1e-3) / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_node": FP64_APPLY_FLOPS_PER_NODE, "ms_per_launch": ms_apply,
+            "peak_kind": "measured FP64 FMA rate (heat_probe_fma_rate, this run)"}
 
 
 def measured_peaks():
@@ -420,6 +454,8 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
             prof = hg.heat_profile_iteration(s.sim, 20, flush)
             torch.cuda.nvtx.range_pop()
         achieved = prof["bytes_apply"] / (prof["ms_apply"] * 1e-3) / 1e9
+        if precision == "fp64":
+            out["fp64_roofline"] = fp64_roofline(hg, p.n_nodes, prof["ms_apply"])
         out[precision] = {"seconds": sec, "ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
                           "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec, "kernel_tuning": tuning,
                           "apply": {"ms_per_launch": prof["ms_apply"], "achieved_gbs": achieved, "peak_gbs": peak,
@@ -572,8 +608,12 @@ def run_serving(hg, nreq: int, rate: float, budget_gb: float):
     import numpy as np
     import workloads as W
     arrivals = W.poisson_arrivals(nreq, rate=rate)
-    ps = [W.serving_request(r) for r in range(nreq)]
-    reqs = [hg.make_request(p) for p in ps]  # inputs prepared before the clock starts
+    reqs, nodes = [], []
+    for r in range(nreq):  # inputs prepared before the clock starts; only the request arrays are kept
+        p = W.serving_request(r)
+        reqs.append(hg.make_request(p))
+        nodes.append(p.n_nodes)
+        del p
     srv = hg.heat_server_create(int(budget_gb * (1 << 30)), 64)
     try:
         t0 = time.perf_counter()
@@ -584,19 +624,64 @@ def run_serving(hg, nreq: int, rate: float, budget_gb: float):
                 time.sleep(ta - now)
             tickets.append(hg.heat_submit(srv, req))
         lat, its_dof = [], 0.0
-        for t, p in zip(tickets, ps):
-            u, st, l = hg.heat_wait(srv, t, p.n_nodes, timeout_s=3600.0)
+        for t, nn in zip(tickets, nodes):
+            u, st, l = hg.heat_wait(srv, t, nn, timeout_s=3600.0)
             lat.append(l)
-            its_dof += p.n_nodes * st["iters"]
+            its_dof += nn * st["iters"]
         wall = time.perf_counter() - t0
         sst = hg.heat_server_get_stats(srv)
     finally:
         hg.heat_destroy_server(srv)
     lat = np.array(lat)
     return {"workload": f"{nreq} requests, Poisson {rate}/s, cubic Q1 20^3..120^3, two-phase k 10:1 at phi U[0.1,0.5], 50..300 steps, dt=1e-3, rtol 1e-8, fp32_refined, HBM budget {budget_gb} GB",
+            "requests": nreq, "arrival_rate_per_s": rate, "arrival_span_s": float(arrivals[-1]),
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "sims_per_s": nreq / wall, "dof_cg_iters_per_s": its_dof / wall, "wall_s": wall,
-            "offered_dof": float(sum(p.n_nodes for p in ps)), "kernel_launches": sst["kernel_launches"]}
+            "offered_dof": float(sum(nodes)), "kernel_launches": sst["kernel_launches"],
+            "failed": sst["failed"]}
+
+
+def run_slab(hg, torch, nsteps: int, stream):
+    """The z-slab split of one simulation (§4.4): the 100^3 inclusions
+    workload's first `nsteps` steps in FP64, unsplit (the tick engine) and
+    split into 1, 2, 4 and 8 slabs on this GPU, in the merged one-reduction
+    iteration and (4 slabs) in Algorithm 1's two-reduction form. Times are
+    CUDA events on the stream; every split field is compared with the
+    unsplit one."""
+    import numpy as np
+    import workloads as W
+    p = W.inclusions_cube(nsteps=nsteps)
+    out = {"workload": f"inclusions_cube_100 (1,030,301 DOF), first {nsteps} steps, FP64, rtol 1e-10"}
+
+    def timed(run):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = run()
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e) / 1e3, st
+
+    with hg.Simulation.from_problem(p, precision="fp64", stream=stream.cuda_stream) as s:
+        s.step(1)
+        hg.heat_set_state(s.sim, p.u0, p.n_nodes)
+        sec, st = timed(lambda: s.step(nsteps))
+        whole = s.state()
+    out["unsplit"] = {"ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
+                      "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec}
+    for ns, merged in ((1, True), (2, True), (4, True), (8, True), (4, False)):
+        with hg.SlabSimulation.from_problem(p, ns, merged=merged, stream=stream.cuda_stream) as s:
+            s.step(1)
+            s.set_state(p.u0)
+            sec, st = timed(lambda: s.step(nsteps))
+            u = s.state()
+        key = f"slabs_{ns}_{'merged' if merged else 'algorithm1'}"
+        out[key] = {"ms_per_step": sec * 1e3 / nsteps, "cg_iterations": st["iters"],
+                    "dof_cg_iters_per_s": p.n_nodes * st["iters"] / sec,
+                    "kernel_launches": st["kernel_launches"],
+                    "field_rel_diff_vs_unsplit": float(np.linalg.norm(u - whole) / np.linalg.norm(whole))}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -637,6 +722,16 @@ def main():
         print(json.dumps({"layered": run_layered(hg, torch, args.layered_steps, stream,
                                                  not (args.no_autotune or args.tuning_json),
                                                  cheb_degrees(args), args.cheb_ratio)}), flush=True)
+        return
+    if args.slab_only:  # the z-slab leg alone
+        print(json.dumps({"z_slabs": run_slab(hg, torch, args.slab_steps, stream)}), flush=True)
+        return
+    if args.serve_only:  # the two serving streams alone
+        out = {"serving": run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
+               if args.serve_requests > 0 else None,
+               "serving_sustainable_rate": run_serving(hg, args.serve_low_requests, args.serve_low_rate,
+                                                       args.serve_budget_gb) if args.serve_low_requests > 0 else None}
+        print(json.dumps(out), flush=True)
         return
     if args.p1_only:  # the six-tetrahedra leg alone (used for profiling captures)
         print(json.dumps({"tetrahedra": run_p1(hg, torch, args.p1_steps, stream)}), flush=True)
@@ -723,8 +818,9 @@ def main():
         b.synchronize()
         t64 = a.elapsed_time(b) / 1e3
         u_ref = sim64.state()
+        prof64 = hg.heat_profile_iteration(sim64.sim, args.profile_reps, flush)
         fp64 = {"value": nn * st64["iters"] / t64, "unit": UNIT, "iters": st64["iters"],
-                "ms_per_forward_solve": t64 * 1e3}
+                "ms_per_forward_solve": t64 * 1e3, "roofline": fp64_roofline(hg, nn, prof64["ms_apply"])}
         sim64.close()
     final_err = None
     if u_ref is not None:
@@ -753,6 +849,11 @@ def main():
         p1 = run_p1(hg, torch, args.p1_steps, stream, tuning["table"] if tuning else None)
     if rank == 0 and args.serve_requests > 0:
         serving = run_serving(hg, args.serve_requests, args.serve_rate, args.serve_budget_gb)
+    serving_low = slab = None
+    if rank == 0 and args.serve_low_requests > 0:
+        serving_low = run_serving(hg, args.serve_low_requests, args.serve_low_rate, args.serve_budget_gb)
+    if rank == 0 and args.slab_steps > 0:
+        slab = run_slab(hg, torch, args.slab_steps, stream)
 
     if rank == 0:
         line = {
@@ -785,6 +886,8 @@ def main():
             "inverse_problem": mh,
             "tetrahedra": p1,
             "serving": serving,
+            "serving_sustainable_rate": serving_low,
+            "z_slabs": slab,
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",

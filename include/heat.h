@@ -272,6 +272,14 @@ heat_status heat_wait(heat_server* srv, uint64_t ticket, double timeout_s, doubl
 heat_status heat_server_get_stats(heat_server* srv, heat_server_stats* out);
 /* Stops the worker; requests not yet finished are abandoned. */
 void heat_destroy_server(heat_server* srv);
+/* Testing hook for the server's recovery (no counterpart in the paper): the
+ * next n engine builds or engine membership updates, of any server, batch or
+ * simulation in the process, fail with HEAT_ERR_NOMEM before touching the
+ * GPU, as a failed device allocation would. When the set a server wants to
+ * run cannot be built, the requests admitted in that round are refused with
+ * that status and the requests already running continue undisturbed. n = 0
+ * clears the hook. */
+heat_status heat_debug_fail_engine_builds(int n);
 
 /* ---- operator-level entry points (device pointers, sim stream) ---------- */
 
@@ -495,6 +503,13 @@ heat_status heat_profile_iteration(heat_sim* sim, int reps, void* flush, size_t 
 heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flush, size_t flush_bytes,
                                          double* ms_apply, double* ms_update,
                                          double* bytes_apply, double* bytes_update);
+
+/* Fused multiply-add throughput of the current GPU (fp64 = 1: FP64, 0: FP32),
+ * TFLOP/s (2 flops per FMA), the best of `reps` timed launches of a kernel
+ * whose threads run independent register-only FMA chains. The ceiling the
+ * FP64 operator passes are measured against: on this GPU FP64 arithmetic,
+ * not memory traffic, bounds them (§5.1 runs the paper's kernels in FP64). */
+heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops);
 
 /* ---- kernel tuning ------------------------------------------------------ */
 

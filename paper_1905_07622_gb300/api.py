@@ -170,6 +170,8 @@ _SIGS = [
     ("heat_slab_step_iterations", C.c_int, [_VP, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
     ("heat_slab_info", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     ("heat_destroy_slab", None, [_VP]),
+    ("heat_probe_fma_rate", C.c_int, [C.c_int, C.c_int, _DP]),
+    ("heat_debug_fail_engine_builds", C.c_int, [C.c_int]),
     ("heat_checks_compiled", C.c_int, []),
     ("heat_check_violations", C.c_int, [_VP, C.POINTER(C.c_uint)]),
     ("heat_last_error", C.c_char_p, []),
@@ -530,6 +532,20 @@ def heat_batch_profile_iteration(batch, reps: int, flush=None):
     _check(_lib.heat_batch_profile_iteration(batch, int(reps), fp, fb, C.byref(ma), C.byref(mu), C.byref(ba),
                                              C.byref(bu)))
     return {"ms_apply": ma.value, "ms_update": mu.value, "bytes_apply": ba.value, "bytes_update": bu.value}
+
+
+def heat_debug_fail_engine_builds(n: int):
+    """Testing hook: the next n engine builds or membership updates fail (HEAT_ERR_NOMEM)."""
+    load_library()
+    _check(_lib.heat_debug_fail_engine_builds(int(n)))
+
+
+def heat_probe_fma_rate(fp64: bool, reps: int = 5) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    load_library()
+    t = C.c_double()
+    _check(_lib.heat_probe_fma_rate(1 if fp64 else 0, int(reps), C.byref(t)))
+    return t.value
 
 
 def heat_tuning_num_variants() -> int:

@@ -8,6 +8,7 @@
 // unfinished simulations every few ticks (the paper's host reads the residual
 // back after every iteration, §3.4.3).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -282,7 +283,19 @@ struct Engine {
   int phases_cap = 0;
   std::vector<SimDev> h_sims;
   std::vector<int2> h_op, h_pw;
+  long long cap_sims = 0;   // simulations the descriptor array holds
+  bool grid_cap = false;    // grids sized by the capacities (members can change without a new graph)
 };
+
+// Host-side fault injection for tests of the server's recovery: the next
+// g_fail_builds engine builds or membership updates return HEAT_ERR_NOMEM.
+static std::atomic<int> g_fail_builds{0};
+static bool injected_failure() {
+  int n = g_fail_builds.load();
+  while (n > 0)
+    if (g_fail_builds.compare_exchange_weak(n, n - 1)) return true;
+  return false;
+}
 
 // Kernels in one tick: k_open, then per iteration the Chebyshev passes and
 // apply + update, or the fused kernel.
@@ -403,11 +416,15 @@ static heat_status engine_upload(Engine* e) {
   int occ_ow = 1;
   if (e->ks.open_w)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ow, e->ks.open_w, 32 * e->ks.owwarps, 0);
-  e->grid_ow = (int)std::max(1LL, std::min<long long>(nwork[3], (long long)sms * std::max(1, occ_ow)));
-  e->grid_op = (int)std::max(1LL, std::min<long long>(nwork[0], (long long)sms * std::max(1, occ_op)));
-  e->grid_pw = (int)std::max(1LL, std::min<long long>(nwork[1], (long long)sms * std::max(1, occ_pw)));
-  e->grid_aw = (int)std::max(1LL, std::min<long long>(nwork[2], (long long)sms * std::max(1, occ_aw)));
-  e->grid_ch = (int)std::max(1LL, std::min<long long>(e->ks.cheb_w ? nwork[2] : nwork[0],
+  // With grid_cap the grids cover the capacities, so a later member set that
+  // fits them runs under the same captured graph (surplus blocks find no item).
+  const long long items[4] = {e->grid_cap ? e->cap_op : nwork[0], e->grid_cap ? e->cap_pw : nwork[1],
+                              e->grid_cap ? e->cap_aw : nwork[2], e->grid_cap ? e->cap_ow : nwork[3]};
+  e->grid_ow = (int)std::max(1LL, std::min<long long>(items[3], (long long)sms * std::max(1, occ_ow)));
+  e->grid_op = (int)std::max(1LL, std::min<long long>(items[0], (long long)sms * std::max(1, occ_op)));
+  e->grid_pw = (int)std::max(1LL, std::min<long long>(items[1], (long long)sms * std::max(1, occ_pw)));
+  e->grid_aw = (int)std::max(1LL, std::min<long long>(items[2], (long long)sms * std::max(1, occ_aw)));
+  e->grid_ch = (int)std::max(1LL, std::min<long long>(e->ks.cheb_w ? items[2] : items[0],
                                                       (long long)sms * std::max(1, occ_ch)));
   return HEAT_OK;
 }
@@ -494,9 +511,11 @@ static heat_status engine_capture(Engine* e) {
 }
 
 heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out,
-                          const Tuning* tun) {
+                          const Tuning* tun, double headroom) {
   *out = nullptr;
   if (nsims < 1 || !sims) return set_error(HEAT_ERR_ARG, "engine: no simulations");
+  if (injected_failure()) return set_error(HEAT_ERR_NOMEM, "engine: build failure injected by the test hook");
+  if (!(headroom >= 1.0) || headroom > 64.0) return set_error(HEAT_ERR_ARG, "engine: headroom must be in [1, 64]");
   Engine* e = new Engine();
   e->sims.assign(sims, sims + nsims);
   e->prec = precision;
@@ -524,6 +543,14 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
     delete e;
     return set_error(HEAT_ERR_ARG, "engine: too many work items");
   }
+  auto grow = [&](long long c) { return (long long)std::ceil((double)c * headroom); };
+  e->cap_sims = grow(nsims);
+  e->grid_cap = headroom > 1.0;
+  cap_op = grow(cap_op);
+  cap_pw = grow(cap_pw);
+  cap_aw = grow(cap_aw);
+  cap_ow = grow(cap_ow);
+  cap_partial = grow(cap_partial);
   e->cap_op = cap_op;
   e->cap_pw = cap_pw;
   e->cap_aw = cap_aw;
@@ -534,7 +561,7 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
     engine_destroy(e);
     return s;
   };
-  if (cudaMalloc(&e->d_sims, sizeof(SimDev) * nsims) != cudaSuccess ||
+  if (cudaMalloc(&e->d_sims, sizeof(SimDev) * e->cap_sims) != cudaSuccess ||
       cudaMalloc(&e->d_work_op, sizeof(int2) * cap_op) != cudaSuccess ||
       cudaMalloc(&e->d_work_pw, sizeof(int2) * cap_pw) != cudaSuccess ||
       cudaMalloc(&e->d_work_aw, sizeof(int2) * std::max(1LL, cap_aw)) != cudaSuccess ||
@@ -604,6 +631,38 @@ heat_status engine_refresh(Engine* e) {
   if (recapture || !e->gexec || e->grid_op != g_op || e->grid_pw != g_pw || e->grid_aw != g_aw || e->grid_ch != g_ch)
     return engine_capture(e);
   return HEAT_OK;
+}
+
+heat_status engine_set_members(Engine* e, heat_sim* const* sims, int nsims) {
+  if (injected_failure()) return set_error(HEAT_ERR_NOMEM, "engine: update failure injected by the test hook");
+  if (nsims < 1 || !sims || nsims > e->cap_sims) return set_error(HEAT_ERR_ARG, "engine: member set exceeds capacity");
+  long long op = 0, pw = 0, aw = 0, ow = 0, part = 0;
+  for (int i = 0; i < nsims; ++i) {
+    const heat_sim* s = sims[i];
+    if (s->prm.precision != e->prec || s->dev.elem != e->elem)
+      return set_error(HEAT_ERR_ARG, "engine: a member's precision or element differs from the engine's");
+    SimDev d = s->dev;
+    tile_geometry(d, e->ks);
+    op += d.ntiles;
+    pw += d.npw;
+    aw += d.w_items;
+    ow += d.o_items;
+    part += std::max(std::max(std::max(d.ntiles, d.npw), d.w_items), d.o_items);
+  }
+  if (op > e->cap_op || pw > e->cap_pw || aw > e->cap_aw || ow > e->cap_ow || part > e->cap_partial)
+    return set_error(HEAT_ERR_ARG, "engine: member set exceeds the work-list capacity");
+  // the last-block counters of newly added members start at zero
+  for (int i = 0; i < nsims; ++i) {
+    heat_sim* s = sims[i];
+    if (std::find(e->sims.begin(), e->sims.end(), s) != e->sims.end()) continue;
+    heat_status st = sim_read_scalars(s);
+    if (st != HEAT_OK) return st;
+    s->h_sc->count = 0;
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) return st;
+  }
+  e->sims.assign(sims, sims + nsims);
+  return engine_refresh(e);
 }
 
 heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters) {
@@ -1002,3 +1061,9 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
 }
 
 }  // namespace heat
+
+extern "C" heat_status heat_debug_fail_engine_builds(int n) {
+  if (n < 0) return heat::set_error(HEAT_ERR_ARG, "heat_debug_fail_engine_builds: n must be >= 0");
+  heat::g_fail_builds.store(n);
+  return HEAT_OK;
+}

@@ -95,8 +95,16 @@ heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter);
 
 // A set of simulations driven together by one captured tick graph (kernel
 // choice from the tuning table, or from `tun` when given).
+// headroom > 1 sizes the descriptor array and work lists for that many times
+// the members' needs and the grids by those capacities, so that
+// engine_set_members can change the members under the same captured graph.
 heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaStream_t stream, Engine** out,
-                          const Tuning* tun = nullptr);
+                          const Tuning* tun = nullptr, double headroom = 1.0);
+// Replace the members (same precision and element) without reallocating:
+// HEAT_ERR_ARG when the set exceeds the engine's capacities (build a new
+// engine then). New members' last-block counters are cleared; the graph is
+// captured again only when the Chebyshev pass count or a grid changes.
+heat_status engine_set_members(Engine* e, heat_sim* const* sims, int nsims);
 void engine_destroy(Engine* e);
 // Re-read the sims' descriptors (after a buffer or parameter change).
 heat_status engine_refresh(Engine* e);

@@ -103,6 +103,12 @@ static void finish_request(heat_server* srv, Req* q, heat_status status) {
   srv->cv_done.notify_all();
 }
 
+// Ticks launched between two reads of the members' phases (and admissions).
+constexpr int kTicksPerPoll = 8;
+// Work-list and descriptor capacity of a server engine relative to the member
+// set it is built for: later sets that fit run under the same captured graph.
+constexpr double kEngineHeadroom = 2.0;
+
 static void worker_loop(heat_server* srv) {
   cudaSetDevice(srv->device);
   if (!srv->stream) {
@@ -112,7 +118,26 @@ static void worker_loop(heat_server* srv) {
   Engine* eng = nullptr;
   long long launches_done = 0;  // of engines already destroyed
   std::vector<int> phases;
-  const int ticks_per_poll = 2;
+  bool members_changed = false;
+  auto active_sims = [&]() {
+    std::vector<heat_sim*> sims;
+    for (Req* q : srv->active) sims.push_back(q->sim);
+    return sims;
+  };
+  // Runs the current active set: the engine takes the new members in place
+  // when they fit its capacities, else a new engine is built.
+  auto rebuild = [&]() -> heat_status {
+    const std::vector<heat_sim*> sims = active_sims();
+    heat_status s = eng ? engine_set_members(eng, sims.data(), (int)sims.size()) : HEAT_ERR_ARG;
+    if (s == HEAT_OK) return s;
+    if (eng) {
+      launches_done += engine_launches(eng);
+      engine_destroy(eng);
+      eng = nullptr;
+    }
+    return engine_create(sims.data(), (int)sims.size(), srv->active[0]->r.params.precision, srv->stream, &eng,
+                         nullptr, kEngineHeadroom);
+  };
   for (;;) {
     // admission: arrival order, first fit by footprint and free slots
     std::vector<Req*> admit;
@@ -145,29 +170,39 @@ static void worker_loop(heat_server* srv) {
         }
       }
     }
-    bool changed = false;
+    std::vector<Req*> added;
     for (Req* q : admit) {
       const heat_status s = start_request(srv, q);
       if (s == HEAT_OK) {
         std::lock_guard<std::mutex> lock(srv->mu);  // `active` is written by this thread only, read under the lock
         srv->active.push_back(q);
-        changed = true;
+        added.push_back(q);
+        members_changed = true;
       } else {
         finish_request(srv, q, s);
       }
     }
     if (srv->active.empty()) continue;
-    if (changed || !eng) {
-      if (eng) {
-        launches_done += engine_launches(eng);
-        engine_destroy(eng);
-        eng = nullptr;
+    if (members_changed || !eng) {
+      heat_status s = rebuild();
+      if (s != HEAT_OK && !added.empty()) {
+        // the new set cannot run: refuse this round's admissions and keep
+        // the requests that were already running
+        const std::string why = heat_last_error();
+        {
+          std::lock_guard<std::mutex> lock(srv->mu);
+          std::vector<Req*> keep;
+          for (Req* q : srv->active)
+            if (std::find(added.begin(), added.end(), q) == added.end()) keep.push_back(q);
+          srv->active.swap(keep);
+        }
+        for (Req* q : added) {
+          q->error = "admission refused: " + why;
+          finish_request(srv, q, s);
+        }
+        s = srv->active.empty() ? HEAT_OK : rebuild();
       }
-      std::vector<heat_sim*> sims;
-      for (Req* q : srv->active) sims.push_back(q->sim);
-      const heat_status s = engine_create(sims.data(), (int)sims.size(), srv->active[0]->r.params.precision,
-                                          srv->stream, &eng);
-      if (s != HEAT_OK) {  // cannot run this set: fail it
+      if (s != HEAT_OK) {  // not even the running set can be run: fail it
         std::vector<Req*> failed;
         {
           std::lock_guard<std::mutex> lock(srv->mu);
@@ -177,24 +212,31 @@ static void worker_loop(heat_server* srv) {
           q->error = heat_last_error();
           finish_request(srv, q, s);
         }
+        if (eng) {
+          launches_done += engine_launches(eng);
+          engine_destroy(eng);
+          eng = nullptr;
+        }
+        members_changed = false;
         continue;
       }
+      members_changed = false;
+      if (srv->active.empty()) continue;
     }
-    heat_status s = engine_launch_ticks(eng, ticks_per_poll);
+    heat_status s = engine_launch_ticks(eng, kTicksPerPoll);
     phases.assign(srv->active.size(), 0);
     if (s == HEAT_OK) s = engine_read_phases(eng, phases.data());
     std::vector<Req*> keep;
-    bool left = false;
     for (size_t i = 0; i < srv->active.size(); ++i) {
       Req* q = srv->active[i];
       if (s != HEAT_OK) {
         q->error = heat_last_error();
         finish_request(srv, q, s);
-        left = true;
+        members_changed = true;
       } else if (phases[i] == PH_DONE || phases[i] == PH_FAILED) {
         heat_status rs = sim_read_scalars(q->sim);
         finish_request(srv, q, rs);
-        left = true;
+        members_changed = true;
       } else {
         keep.push_back(q);
       }
@@ -203,11 +245,6 @@ static void worker_loop(heat_server* srv) {
       std::lock_guard<std::mutex> lock(srv->mu);
       srv->active.swap(keep);
       srv->st.kernel_launches = launches_done + (eng ? engine_launches(eng) : 0);
-    }
-    if (left && eng) {  // membership changes before the next tick
-      launches_done += engine_launches(eng);
-      engine_destroy(eng);
-      eng = nullptr;
     }
   }
   if (eng) engine_destroy(eng);
@@ -269,7 +306,9 @@ extern "C" heat_status heat_submit(heat_server* srv, const heat_request* req, ui
   q->k.assign(req->k, req->k + q->ne);
   if (req->u0) q->u0.assign(req->u0, req->u0 + q->nn);
   q->r.rho_c = q->r.k = q->r.u0 = nullptr;
-  q->footprint = sim_footprint(q->nn, q->ne) + engine_footprint(q->nn, req->nx, req->ny, req->nz);
+  // the server's engines hold kEngineHeadroom times each member's work lists
+  q->footprint = sim_footprint(q->nn, q->ne) +
+                 (size_t)(kEngineHeadroom * (double)engine_footprint(q->nn, req->nx, req->ny, req->nz));
   std::lock_guard<std::mutex> lock(srv->mu);
   if (q->footprint > srv->budget) {
     delete q;

@@ -109,3 +109,41 @@ def test_rejections_and_bounded_wait():
         assert e.value.status == hg.HEAT_ERR_TIMEOUT
     finally:
         hg.heat_destroy_server(srv)  # abandons the running request without hanging
+
+
+def test_admission_that_cannot_be_built_leaves_running_requests_unchanged():
+    """A request admitted while another runs, whose member set cannot be
+    built (a failed device allocation, injected on the host), is refused;
+    the running request finishes bitwise as it would alone, and the next
+    request is served normally."""
+    import paper_1905_07622_gb300 as hg
+    p_long = W.random_box(16, 16, 16, seed=31, flux={5: 1.0}, nsteps=600, rtol=1e-10)
+    p_new = W.random_box(10, 10, 10, seed=32, flux={5: 1.0}, nsteps=5, rtol=1e-10)
+    srv = hg.heat_server_create(4 * GB, 8)
+    try:
+        r1, k1 = hg.make_request(p_long, precision="fp32_refined")
+        t1 = hg.heat_submit(srv, r1)
+        t0 = time.time()
+        while hg.heat_server_get_stats(srv)["active"] < 1:
+            assert time.time() - t0 < 60
+            time.sleep(0.001)
+        hg.heat_debug_fail_engine_builds(1)
+        r2, k2 = hg.make_request(p_new, precision="fp32_refined")
+        t2 = hg.heat_submit(srv, r2)
+        with pytest.raises(hg.HeatError) as e:
+            hg.heat_wait(srv, t2, p_new.n_nodes, timeout_s=120.0)
+        assert e.value.status == hg.HEAT_ERR_NOMEM
+        still_running = not hg.heat_poll(srv, t1)
+        u1, st1, _ = hg.heat_wait(srv, t1, p_long.n_nodes, timeout_s=300.0)
+        r3, k3 = hg.make_request(p_new, precision="fp32_refined")
+        t3 = hg.heat_submit(srv, r3)
+        u3, _, _ = hg.heat_wait(srv, t3, p_new.n_nodes, timeout_s=120.0)
+        stats = hg.heat_server_get_stats(srv)
+    finally:
+        hg.heat_debug_fail_engine_builds(0)
+        hg.heat_destroy_server(srv)
+    assert still_running  # the refusal happened while the long request ran
+    assert st1["steps"] == p_long.nsteps
+    assert np.array_equal(u1, _alone(p_long))
+    assert np.array_equal(u3, _alone(p_new))
+    assert stats["failed"] == 1 and stats["completed"] == 2

@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -90,14 +91,57 @@ def parse():
     ap.add_argument("--tuning-json", default="",
                     help='set the kernel tuning table instead of autotuning, e.g. '
                          '\'{"variant": [-1, 1, 0], "seg_nodes": [2048, 1024, 512]}\'')
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="time the oracle's C solver on every configuration (host only) and exit")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- oracle leg
 
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def c_oracle_steps(p, S, nsteps: int, threads: int, max_iter: int = 20000):
+    """The oracle's C Jacobi-PCG (Algorithm 1) over the first nsteps steps:
+    (seconds in the solver, CG iterations). Right-hand sides (sparse products
+    in the Python oracle) are formed outside the timed solver calls."""
+    import numpy as np
+    from oracle import cpu, transient
+    A = cpu.CSR(S.A_ff)
+    u_prev, u_prev2 = p.u0.copy(), None
+    u_prev[S.dir_ids] = S.dir_vals
+    sec, its = 0.0, 0
+    for n in range(1, nsteps + 1):
+        b = transient.step_rhs(p, S, u_prev, n)
+        x0 = (u_prev if u_prev2 is None else 2.0 * u_prev - u_prev2)[S.free]
+        t0 = time.perf_counter()
+        x, it, _, _ = cpu.pcg(A, b, x0, S.pinv_f, p.rtol, max_iter=max_iter, threads=threads)
+        sec += time.perf_counter() - t0
+        its += it
+        u = np.empty(p.n_nodes)
+        u[S.free] = x
+        u[S.dir_ids] = S.dir_vals
+        u_prev2, u_prev = u_prev, u
+    return sec, its
+
+
 def cpu_worker(nsteps_sample: int):
-    """Runs in a fresh 1-thread process: oracle PCG on the first time steps."""
+    """Runs in a fresh process before the GPU is touched: the oracle on the
+    first time steps of the headline workload, in Python (SciPy CSR, one
+    thread), in C on one thread, and in C on every host core; then the
+    incomplete-Cholesky context."""
     import workloads as W
     from oracle import transient
 
@@ -107,33 +151,94 @@ def cpu_worker(nsteps_sample: int):
     res = transient.run(p, solver="pcg", nsteps=nsteps_sample, system=S)
     dt = time.perf_counter() - t0
     it = sum(res.iters)
-    out = {"seconds": dt, "iters": it, "dof": p.n_nodes, "steps": nsteps_sample, "value": p.n_nodes * it / dt}
-    out["incomplete_factorisation"] = ilu_context()
+    cores, model = host_cpu()
+    out = {"python": {"seconds": dt, "iters": it, "value": p.n_nodes * it / dt, "threads": 1},
+           "dof": p.n_nodes, "steps": nsteps_sample, "nproc": cores, "cpu_model": model}
+    for key, th in (("c_one_core", 1), ("c_all_cores", cores)):
+        sec, its = c_oracle_steps(p, S, nsteps_sample, th)
+        out[key] = {"seconds": sec, "iters": its, "value": p.n_nodes * its / sec, "threads": th}
+    out["incomplete_factorisation"] = ic_context()
     print(json.dumps(out))
 
 
-def ilu_context(n: int = 40):
-    """The paper's CPU comparison solver, PCG with an incomplete factorisation
-    of drop tolerance 1e-3 (SuperLU's ILU standing in for incomplete
-    Cholesky), against the oracle's Jacobi-PCG on the first step of the
-    inclusions workload at n^3 elements (context only, one thread)."""
-    from oracle import pcg, precond, transient
+def ic_context(n: int = 40):
+    """The paper's CPU comparison solver (§5.2, Table 2): CG preconditioned by
+    an incomplete Cholesky factorisation of drop tolerance 1e-3, in the
+    oracle's plain C, against the oracle's C Jacobi-PCG, on the first step of
+    the inclusions workload at n^3 elements (context only, one thread)."""
+    from oracle import cpu, transient
     import workloads as W
 
     p = W.inclusions_cube(n=n)
     S = transient.build_system(p)
     b = transient.step_rhs(p, S, p.u0, 1)
     x0 = p.u0[S.free]
+    A = cpu.CSR(S.A_ff)
     t0 = time.perf_counter()
-    M = precond.ilu_preconditioner(S.A_ff, drop_tol=1e-3)
+    F = cpu.IC(A, 1e-3)
     t1 = time.perf_counter()
-    _, it_ilu = precond.pcg_precond(S.A_ff, b, x0, M, p.rtol)
+    _, it_ic, _, _ = cpu.pcg_ic(A, b, x0, S.pinv_f, F, p.rtol)
     t2 = time.perf_counter()
-    _, it_jac, _, _ = pcg.pcg(S.A_ff, b, x0, S.pinv_f, p.rtol)
+    _, it_jac, _, _ = cpu.pcg(A, b, x0, S.pinv_f, p.rtol, threads=1)
     t3 = time.perf_counter()
     return {"sample": f"inclusions_cube_{n} ({p.n_nodes} DOF), step 1, rtol {p.rtol:g}", "drop_tol": 1e-3,
-            "factorisation_s": t1 - t0, "ilu_pcg": {"iterations": it_ilu, "solve_s": t2 - t1},
+            "factorisation": "incomplete Cholesky, drop |l_ik| < 1e-3 ||A(k:n,k)||_1 (oracle/cpcg.c)",
+            "factorisation_s": t1 - t0, "factor_nnz_per_row": F.nnz / S.free.size,
+            "ic_pcg": {"iterations": it_ic, "solve_s": t2 - t1},
             "jacobi_pcg": {"iterations": it_jac, "solve_s": t3 - t2}, "cores": 1}
+
+
+def cpu_config_timings():
+    """--cpu-configs: the oracle's C Jacobi-PCG on every configuration's
+    workload, one thread and every host core, with the truncation stated:
+    the 16^3 two-phase cube (all 20 steps), the 100^3 inclusions cube (first
+    3 steps), one 40^3 log-normal batch member (first 20 of 150 steps), and
+    the 200^3 layered cube (the first 100 CG iterations of step 1, on the
+    eliminated operator padded with identity rows, assembled in stencil form).
+    Prints one JSON line."""
+    import numpy as np
+    import scipy.sparse as sp
+    import workloads as W
+    from oracle import cpu, fem, transient
+    cores, model = host_cpu()
+    out = {"nproc": cores, "cpu_model": model, "configs": {}}
+    cases = [("1 two_phase_cube 16^3", W.two_phase_cube(), None, "all 20 steps"),
+             ("2 inclusions_cube 100^3", W.inclusions_cube(), 3, "first 3 of 300 steps"),
+             ("3 lognormal_cube 40^3 (one member)", W.lognormal_cube(0), 20, "first 20 of 150 steps")]
+    for name, p, nsteps, trunc in cases:
+        S = transient.build_system(p)
+        ns = nsteps or p.nsteps
+        row = {"dof": p.n_nodes, "truncation": trunc}
+        for key, th in (("one_core", 1), ("all_cores", cores)):
+            sec, its = c_oracle_steps(p, S, ns, th)
+            row[key] = {"threads": th, "seconds": sec, "cg_iterations": its, "ms_per_iteration": 1e3 * sec / its,
+                        "dof_cg_iters_per_s": p.n_nodes * its / sec, "ms_per_step": 1e3 * sec / ns}
+        out["configs"][name] = row
+        print(json.dumps({name: row}), file=sys.stderr, flush=True)
+    # 200^3 layered: step 1's system, truncated to 100 iterations
+    p = W.layered_cube(nsteps=1)
+    A = fem.assemble_stencil(p, 1.0 / p.dt, p.theta)
+    dn, dv = fem.dirichlet_nodes(p)
+    mask = np.ones(p.n_nodes)
+    mask[dn] = 0.0
+    D = sp.diags(mask)
+    Ap = (D @ A @ D + sp.diags(1.0 - mask)).tocsr()
+    g = np.zeros(p.n_nodes)
+    g[dn] = dv
+    b = fem.apply_all(p, p.u0, 1.0 / p.dt, p.theta - 1.0, eliminate=False) - fem.apply_all(
+        p, g, 1.0 / p.dt, p.theta, eliminate=False)
+    b *= mask
+    pinv = 1.0 / Ap.diagonal()
+    M = cpu.CSR(Ap)
+    row = {"dof": p.n_nodes, "truncation": "first 100 CG iterations of step 1 (of about 1,400)"}
+    for key, th in (("one_core", 1), ("all_cores", cores)):
+        t0 = time.perf_counter()
+        _, its, _, _ = cpu.pcg(M, b, np.zeros(p.n_nodes), pinv, 1e-30, max_iter=100, threads=th)
+        sec = time.perf_counter() - t0
+        row[key] = {"threads": th, "seconds": sec, "cg_iterations": its, "ms_per_iteration": 1e3 * sec / its,
+                    "dof_cg_iters_per_s": p.n_nodes * its / sec}
+    out["configs"]["5 layered_cube 200^3"] = row
+    print(json.dumps(out), flush=True)
 
 
 def run_cpu_baseline(nsteps_sample: int):
@@ -316,16 +421,19 @@ def aggregate(world, seconds: float, units: float):
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
-    """The oracle (plain FP64 CSR Jacobi-PCG, 1 host thread), each step one time step."""
+    """The oracle (plain FP64 CSR Jacobi-PCG in C, OpenMP on every host core),
+    each bench step one time step of the headline workload."""
     if rank != 0:
         return
+    import numpy as np
     import workloads as W
-    from oracle import transient
+    from oracle import cpu, transient
 
     p = W.inclusions_cube()
     S = transient.build_system(p)
+    A = cpu.CSR(S.A_ff)
+    cores, model = host_cpu()
     u_prev, u_prev2 = p.u0.copy(), None
-    from oracle import pcg
     times, iters = [], []
     n = 0
     for k in range(args.warmup + args.steps):
@@ -333,9 +441,11 @@ def run_reference(args, world, rank):
         t0 = time.perf_counter()
         b = transient.step_rhs(p, S, u_prev, n)
         x0 = u_prev if u_prev2 is None else 2 * u_prev - u_prev2
-        x, it, _, _ = pcg.pcg(S.A_ff, b, x0[S.free], S.pinv_f, p.rtol)
+        x, it, _, _ = cpu.pcg(A, b, x0[S.free], S.pinv_f, p.rtol, threads=cores)
         dt = time.perf_counter() - t0
-        u_new = x
+        u_new = np.empty(p.n_nodes)
+        u_new[S.free] = x
+        u_new[S.dir_ids] = S.dir_vals
         u_prev2, u_prev = u_prev, u_new
         if k >= args.warmup:
             times.append(dt)
@@ -347,9 +457,8 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (host)",
                                             "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1") or 1),
-                             "kind": "oracle",
-                             "sample": f"steps 1..{args.warmup + args.steps} of the 300-step transient, one per bench step; assembly untimed"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"steps 1..{args.warmup + args.steps} of the 300-step transient, one per bench step (right-hand side in SciPy, Jacobi-PCG in the oracle's C on {cores} threads of {model}); assembly untimed"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "iters": iters}
     print(json.dumps(line), flush=True)
@@ -688,6 +797,9 @@ def run_slab(hg, torch, nsteps: int, stream):
 
 def main():
     args = parse()
+    if args.cpu_configs:
+        cpu_config_timings()
+        return
     if args.cpu_worker:
         cpu_worker(args.cpu_worker)
         return
@@ -890,9 +1002,19 @@ def main():
             "z_slabs": slab,
         }
         if cpu is not None:
-            line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"oracle Jacobi-PCG, first {cpu['steps']} time steps of the same workload ({cpu['iters']} CG iterations, {cpu['seconds']:.1f} s; CSR assembly untimed)",
-                                    "incomplete_factorisation_context": cpu.get("incomplete_factorisation")}
+            c = cpu["c_all_cores"]
+            line["cpu_baseline"] = {
+                "value": c["value"], "unit": UNIT, "cores": c["threads"], "kind": "oracle",
+                "sample": (f"the oracle's C Jacobi-PCG (Algorithm 1, CSR, OpenMP on {c['threads']} threads of "
+                           f"{cpu['cpu_model']}), first {cpu['steps']} time steps of the same workload "
+                           f"({c['iters']} CG iterations, {c['seconds']:.2f} s in the solver; assembly and "
+                           "right-hand sides untimed)"),
+                "nproc": cpu["nproc"], "cpu_model": cpu["cpu_model"],
+                "one_core": {"value": cpu["c_one_core"]["value"], "seconds": cpu["c_one_core"]["seconds"],
+                             "kind": "oracle, C, 1 thread (the paper's one-core baseline)"},
+                "python_one_core": {"value": cpu["python"]["value"], "seconds": cpu["python"]["seconds"],
+                                    "kind": "oracle, NumPy/SciPy CSR, 1 thread"},
+                "incomplete_cholesky_context": cpu.get("incomplete_factorisation")}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:

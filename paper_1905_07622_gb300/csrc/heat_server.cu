@@ -129,7 +129,9 @@ static void worker_loop(heat_server* srv) {
   auto rebuild = [&]() -> heat_status {
     const std::vector<heat_sim*> sims = active_sims();
     heat_status s = eng ? engine_set_members(eng, sims.data(), (int)sims.size()) : HEAT_ERR_ARG;
-    if (s == HEAT_OK) return s;
+    // a new engine only when the set outgrew this one's capacities; any other
+    // failure means the set cannot run
+    if (s == HEAT_OK || (eng && s != HEAT_ERR_ARG)) return s;
     if (eng) {
       launches_done += engine_launches(eng);
       engine_destroy(eng);

@@ -113,3 +113,15 @@ def test_pins_catch_planted_mistakes():
             assert np.linalg.norm(bad - ref) <= 1e-14 * np.linalg.norm(ref)
     finally:
         fem._layer_connectivity = orig
+
+
+@pytest.mark.parametrize("dims,extent", [((5, 4, 6), (1.0, 0.5, 2.0)), ((3, 7, 2), (0.3, 1.0, 1.0)),
+                                         ((8, 8, 8), (1.0, 1.0, 1.0))])
+def test_stencil_assembly_equals_coo_assembly(dims, extent):
+    p = W.random_box(*dims, seed=13, extent=extent, contrast=(0.01, 100.0))
+    M = fem.assemble(p.nx, p.ny, p.nz, p.extent, p.rho_c, "M")
+    K = fem.assemble(p.nx, p.ny, p.nz, p.extent, p.k, "K")
+    for sa, sb in ((1.0, 0.0), (0.0, 1.0), (1 / 0.003, 0.5), (1 / 0.003, -0.5)):
+        A = (sa * M + sb * K).tocsr()
+        B = fem.assemble_stencil(p, sa, sb, layers=3)
+        assert abs(A - B).max() <= 1e-14 * abs(A).max()

@@ -15,7 +15,7 @@
 #include <type_traits>
 
 #include "engine.h"
-#include "tile_kernels.cuh"
+#include "open_kernels.cuh"
 
 namespace heat {
 

@@ -526,11 +526,12 @@ heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops);
  *     (N < 200000, N < 4000000, larger); 32 .. 2^20, default 512.
  *   pw_quads[p]: for heat_precision p, groups of 4 nodes each thread of the
  *     pointwise update kernel handles (1, 2 or 4; default {2, 4, 4}).
- *   open_w[p]: for heat_precision p, 1 runs the step-start and refinement
- *     residual passes (§3.1's right-hand side, the true residual of
- *     Algorithm 1 and of the refinement) in the warp-segment march with
- *     two-row segments, 0 in block tiles (default {0, 0, 0}; trilinear boxes
- *     only, six-tetrahedra boxes always use block tiles). */
+ *   open_w[p]: for heat_precision p, how the step-start and refinement
+ *     residual passes run (§3.1's right-hand side, the true residual of
+ *     Algorithm 1 and of the refinement): 0 in block tiles, 1 in the
+ *     warp-segment march with two-row segments, 2 with one-row segments
+ *     (default {0, 0, 0}; trilinear boxes only, six-tetrahedra boxes always
+ *     use block tiles). */
 typedef struct heat_tuning {
   int variant[3];
   int seg_nodes[3];

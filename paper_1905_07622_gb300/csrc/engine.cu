@@ -41,15 +41,25 @@ struct KernelSet {
   int owsx = 0, owny = 0, owwarps = 0;
 };
 
-// The warp-segment form of k_open for precision prec: 32-lane segments of 2
-// rows, 4 warps per block (double-float on the FP32 paths, FP64 on the FP64
-// path; the two-row segment keeps the double-width values in registers).
-constexpr int kOpenSX = 32, kOpenNY = 2, kOpenWarps = 4;
-static TileFn open_w_kernel(int prec) {
+// The warp-segment forms of k_open (tuning open_w): 32-lane segments of 2
+// rows (shape 1) or 1 row (shape 2), 4 warps per block; double-float on the
+// FP32 paths, FP64 on the FP64 path. Two rows hold twice the double-width
+// values of a lane (254 registers, 2 blocks per SM); one row fits 168
+// registers and 3 blocks per SM at the cost of more halo rows per output.
+constexpr int kOpenSX = 32, kOpenWarps = 4;
+static int open_w_rows(int shape) { return shape == 2 ? 1 : 2; }
+static TileFn open_w_kernel(int prec, int shape) {
+  if (shape == 2) {
+    switch (prec) {
+      case P_FP64: return k_open_w<P_FP64, kOpenSX, 1, kOpenWarps, 3>;
+      case P_FP32_REFINED: return k_open_w<P_FP32_REFINED, kOpenSX, 1, kOpenWarps, 3>;
+      default: return k_open_w<P_FP32_PLAIN, kOpenSX, 1, kOpenWarps, 3>;
+    }
+  }
   switch (prec) {
-    case P_FP64: return k_open_w<P_FP64, kOpenSX, kOpenNY, kOpenWarps, 1>;
-    case P_FP32_REFINED: return k_open_w<P_FP32_REFINED, kOpenSX, kOpenNY, kOpenWarps, 2>;
-    default: return k_open_w<P_FP32_PLAIN, kOpenSX, kOpenNY, kOpenWarps, 2>;
+    case P_FP64: return k_open_w<P_FP64, kOpenSX, 2, kOpenWarps, 1>;
+    case P_FP32_REFINED: return k_open_w<P_FP32_REFINED, kOpenSX, 2, kOpenWarps, 2>;
+    default: return k_open_w<P_FP32_PLAIN, kOpenSX, 2, kOpenWarps, 2>;
   }
 }
 
@@ -158,8 +168,8 @@ heat_status tuning_set(const Tuning& t) {
     if (t.pw_quads[p] != 1 && t.pw_quads[p] != 2 && t.pw_quads[p] != 4)
       return set_error(HEAT_ERR_ARG, "tuning: pointwise groups %d not 1, 2 or 4", t.pw_quads[p]);
   for (int p = 0; p < 3; ++p)
-    if (t.open_w[p] != 0 && t.open_w[p] != 1)
-      return set_error(HEAT_ERR_ARG, "tuning: open_w[%d] = %d not 0 or 1", p, t.open_w[p]);
+    if (t.open_w[p] < 0 || t.open_w[p] > 2)
+      return set_error(HEAT_ERR_ARG, "tuning: open_w[%d] = %d not 0, 1 or 2", p, t.open_w[p]);
   for (int b = 0; b < 3; ++b)
     if (t.seg_nodes[b] < 32 || t.seg_nodes[b] > (1 << 20))
       return set_error(HEAT_ERR_ARG, "tuning: segment size %d out of range", t.seg_nodes[b]);
@@ -219,9 +229,9 @@ static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int el
     }
   }
   if (elem == E_Q1 && t.open_w[prec]) {
-    k.open_w = open_w_kernel(prec);
+    k.open_w = open_w_kernel(prec, t.open_w[prec]);
     k.owsx = kOpenSX;
-    k.owny = kOpenNY;
+    k.owny = open_w_rows(t.open_w[prec]);
     k.owwarps = kOpenWarps;
   }
   for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];

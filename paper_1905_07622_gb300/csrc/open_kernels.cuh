@@ -76,9 +76,9 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
               const double v = u1[m];  // the staged input, read back in FP64
               x[m] = hp ? 2.0 * v - u2[m] : v;
               const double rn = bn - (hp ? 2.0 * y1[m] - y2[m] : y1[m]);
-              const float r32 = df_d2f(rn);
+              const float r32 = (float)rn;
               r32out[m] = r32;
-              part[2] += df_f2d(r32 * r32 * s.pinv32[m]);
+              part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
               part[0] += rn * rn * pinv[m];
             }
           }
@@ -102,9 +102,9 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
           if (P == P_FP64) {
             s.r[m] = rn;
           } else {
-            const float r32 = df_d2f(rn);
+            const float r32 = (float)rn;
             r32out[m] = r32;
-            part[2] += df_f2d(r32 * r32 * s.pinv32[m]);
+            part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
           }
           part[0] += rn * rn * pinv[m];
         });
@@ -117,7 +117,7 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
     op(inv_dt, theta, true,
         [&](int m, bool live) -> D2 {
           if (!live) return {0.0, 0.0};
-          return {x[m], df_f2d(e32[m])};
+          return {x[m], (double)e32[m]};
         },
         [](const D2& r) { return r.a + r.b; },
         [&](int m, bool dir, TO yo, TO) {
@@ -126,13 +126,13 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
           if (dir) {
             xa[m] = dval(m);
           } else {
-            xa[m] = x[m] + df_f2d(e32[m]);  // the staged input, formed again in FP64
+            xa[m] = x[m] + (double)e32[m];  // the staged input, formed again in FP64
             ya[m] = y;
             rn = b[m] - y;
           }
-          const float r32 = df_d2f(rn);
+          const float r32 = (float)rn;
           r32out[m] = r32;
-          part[2] += df_f2d(r32 * r32 * s.pinv32[m]);
+          part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
           part[0] += rn * rn * pinv[m];
         });
   } else {  // PH_RESID (FP64): r = b - A' x, x already advanced by k_update

@@ -104,7 +104,7 @@ def test_tuning_table_host_logic(lib):
         for quads in ([3, 4, 4], [2, 0, 4], [2, 4, 8]):
             with pytest.raises(api.HeatError):
                 api.heat_tuning_set([-1, 0, 0], [512] * 3, quads)
-        for ow in ([2, 1, 1], [0, -1, 1]):
+        for ow in ([3, 1, 1], [0, -1, 1]):
             with pytest.raises(api.HeatError):
                 api.heat_tuning_set([-1, 0, 0], [512] * 3, [2, 4, 4], ow)
         # a rejected table leaves the last good one in place

@@ -182,8 +182,9 @@ def test_batch_autotune_rebuilds_and_keeps_parity():
         assert np.linalg.norm(g - ref.u[2]) <= 1e-8 * np.linalg.norm(ref.u[2])
 
 
+@pytest.mark.parametrize("shape", [1, 2])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
-def test_warp_segment_open_passes_match_block_tiles_and_oracle(precision):
+def test_warp_segment_open_passes_match_block_tiles_and_oracle(precision, shape):
     """The step-start and refinement passes in the warp-segment march
     (tuning open_w = 1) give the block-tile passes' fields and the oracle's."""
     import paper_1905_07622_gb300 as hg
@@ -194,7 +195,7 @@ def test_warp_segment_open_passes_match_block_tiles_and_oracle(precision):
     old = hg.heat_tuning_get()
     fields = {}
     try:
-        for ow in (0, 1):
+        for ow in (0, shape):
             hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], [ow, ow, ow])
             with hg.Simulation.from_problem(p, precision=precision) as s:
                 us = []
@@ -206,6 +207,6 @@ def test_warp_segment_open_passes_match_block_tiles_and_oracle(precision):
         hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"])
     tol = 1e-9 if precision == "fp64" else 1e-8
     for n in range(p.nsteps):
-        a, b = fields[0][n], fields[1][n]
+        a, b = fields[0][n], fields[shape][n]
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a), n
         assert np.linalg.norm(b - ref.u[n + 1]) <= tol * np.linalg.norm(ref.u[n + 1]), n

@@ -530,8 +530,9 @@ heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops);
  *     residual passes run (§3.1's right-hand side, the true residual of
  *     Algorithm 1 and of the refinement): 0 in block tiles, 1 in the
  *     warp-segment march with two-row segments, 2 with one-row segments
- *     (default {0, 0, 0}; trilinear boxes only, six-tetrahedra boxes always
- *     use block tiles). */
+ *     (default {2, 2, 2}; trilinear boxes only, six-tetrahedra boxes always
+ *     use block tiles). On trilinear boxes the passes of the A operator read
+ *     each element's precomputed Walsh-pair coefficients. */
 typedef struct heat_tuning {
   int variant[3];
   int seg_nodes[3];

@@ -135,7 +135,7 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // variant per precision (-1: the block-tile apply) and the segment tile size
 // per mesh-size bucket. Both are fixed per simulation size, so results stay
 // bitwise identical alone and in batches built under the same table.
-static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}, {0, 0, 0}};
+static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}, {2, 2, 2}};
 static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }

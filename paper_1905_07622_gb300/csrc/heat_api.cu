@@ -366,6 +366,7 @@ extern "C" heat_status heat_sim_create(const heat_mesh* mesh, const heat_bc* bc,
   field = (type)p;
   ALLOC(d.coef, (size_t)s->ne * sizeof(double2), const double2*);
   ALLOC(d.coef32, (size_t)s->ne * sizeof(float2), const float2*);
+  ALLOC(d.acoef, (size_t)s->ne * 4 * sizeof(float4), const float4*);
   for (int v = 0; v < 4; ++v) { ALLOC(d.vec64[v], N8, double*); }
   for (int v = 0; v < 4; ++v) { ALLOC(d.yv[v], N8, double*); }
   ALLOC(d.b, N8, double*);
@@ -652,8 +653,9 @@ heat_status heat::sim_prepare_steps(heat_sim* s, int nsteps) {
 }
 
 size_t heat::sim_footprint(long long nn, long long ne) {
-  // 16 FP64 and 10 FP32 node vectors, FP64 and FP32 coefficient pairs, scalars
-  return (size_t)nn * (16 * 8 + 10 * 4) + (size_t)ne * (16 + 8) + sizeof(SimDev) + sizeof(SimScalars) +
+  // 16 FP64 and 10 FP32 node vectors, FP64 and FP32 coefficient pairs, the
+  // A operator's per-element Walsh-pair coefficients (64 bytes), scalars
+  return (size_t)nn * (16 * 8 + 10 * 4) + (size_t)ne * (16 + 8 + 64) + sizeof(SimDev) + sizeof(SimScalars) +
          4096 * sizeof(int) + 1024;
 }
 

@@ -145,6 +145,11 @@ struct alignas(16) SimDev {  // 16-byte aligned: blocks copy it with uint4 loads
   // V / h_a^2 (a = x, y, z) with V = hx hy hz / 6
   double p1c[4];
   float p1c_f[4];
+  // Trilinear boxes: per element the A operator's (sa = 1/dt, sb = theta)
+  // Walsh-pair coefficients A_q, B_q (q = 0..3) of the factorised form
+  // (op.cuh), 64 bytes each: FP64 on the FP64 path, double-float pairs on
+  // the FP32 paths (the arithmetic of their step-start and refinement passes).
+  const float4* acoef;
   double* partial;            // 2 per tile
   int* iters_log;             // CG iterations of each step
   int iters_log_len;

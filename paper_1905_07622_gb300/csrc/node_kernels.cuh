@@ -181,6 +181,10 @@ __global__ void k_setup_lift(const SimDev* __restrict__ sp) {
 }
 
 // FP32 copy of the coefficients; counts non-finite or non-positive entries.
+// On trilinear boxes also the A operator's per-element Walsh-pair
+// coefficients (SimDev::acoef): A_q = rc/dt (lm_q + lm_{q+4}) + theta k
+// (lk_q + lk_{q+4}), B_q the same with differences, computed in FP64 and
+// stored as FP64 (FP64 path) or as (hi, lo) float pairs (FP32 paths).
 __global__ void k_setup_coef32(const SimDev* __restrict__ sp, long long ne, unsigned int* bad) {
   const SimDev& s = *sp;
   unsigned int nbad = 0;
@@ -189,6 +193,31 @@ __global__ void k_setup_coef32(const SimDev* __restrict__ sp, long long ne, unsi
     const double2 c = s.coef[e];
     if (!(isfinite(c.x) && isfinite(c.y) && c.x > 0.0 && c.y > 0.0)) ++nbad;
     reinterpret_cast<float2*>(const_cast<float2*>(s.coef32))[e] = make_float2((float)c.x, (float)c.y);
+    if (s.acoef && s.elem == E_Q1) {
+      const double a = s.inv_dt * c.x, b = s.theta * c.y;
+      double A[4], B[4];
+      for (int q = 0; q < 4; ++q) {
+        A[q] = a * (s.lam_m[q] + s.lam_m[q + 4]) + b * (s.lam_k[q] + s.lam_k[q + 4]);
+        B[q] = a * (s.lam_m[q] - s.lam_m[q + 4]) + b * (s.lam_k[q] - s.lam_k[q + 4]);
+      }
+      float4* out = const_cast<float4*>(s.acoef) + 4 * e;
+      if (s.prec == P_FP64) {
+        double2* o = reinterpret_cast<double2*>(out);
+        o[0] = make_double2(A[0], A[1]);
+        o[1] = make_double2(A[2], A[3]);
+        o[2] = make_double2(B[0], B[1]);
+        o[3] = make_double2(B[2], B[3]);
+      } else {
+        float h[8], l[8];
+        for (int q = 0; q < 4; ++q) {
+          h[q] = (float)A[q];
+          l[q] = (float)(A[q] - (double)h[q]);
+          h[q + 4] = (float)B[q];
+          l[q + 4] = (float)(B[q] - (double)h[q + 4]);
+        }
+        for (int w = 0; w < 4; ++w) out[w] = make_float4(h[2 * w], l[2 * w], h[2 * w + 1], l[2 * w + 1]);
+      }
+    }
   }
   if (nbad) atomicAdd(bad, nbad);
 }

@@ -18,6 +18,7 @@
 //    after waiting for its own copy groups).
 #pragma once
 
+#include <type_traits>
 #include <utility>
 
 #include "op.cuh"
@@ -54,6 +55,41 @@ template <> struct Pair2<DF> {
   static __device__ __forceinline__ DF2 mul(DF2 a, DF2 b) { return DF2{a.x * b.x, a.y * b.y}; }
   static __device__ __forceinline__ DF2 fma(DF2 a, DF2 b, DF2 c) { return DF2{a.x * b.x + c.x, a.y * b.y + c.y}; }
 };
+
+// One element's precomputed Walsh-pair coefficients A_0..A_3, B_0..B_3 of the
+// A operator (SimDev::acoef): FP64 pairs, or (hi, lo) float pairs for DF.
+struct alignas(16) PreRec {
+  float4 w[4];
+};
+
+// The march's per-element pair coefficients (A_q, B_q) for the pair halves
+// h = 0 (q = 0, 1) and h = 1 (q = 2, 3): formed from the element's (rho_c,
+// k) and the scaled eigenvalue sums AM, AK, BM, BK, or read from a PreRec.
+template <class T, class C, class T2>
+__device__ __forceinline__ void march_coeffs(const C& cf, const T2 (&AM)[2], const T2 (&AK)[2], const T2 (&BM)[2],
+                                             const T2 (&BK)[2], T2 (&A)[2], T2 (&B)[2]) {
+  using V = Pair2<T>;
+  const T2 rc = V::make(cf.x, cf.x), kc = V::make(cf.y, cf.y);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    A[h] = V::fma(kc, AK[h], V::mul(rc, AM[h]));
+    B[h] = V::fma(kc, BK[h], V::mul(rc, BM[h]));
+  }
+}
+template <class T, class T2>
+__device__ __forceinline__ void march_coeffs(const PreRec& cf, const T2 (&)[2], const T2 (&)[2], const T2 (&)[2],
+                                             const T2 (&)[2], T2 (&A)[2], T2 (&B)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, DF>::value) {
+      A[h] = *reinterpret_cast<const T2*>(&cf.w[h]);
+      B[h] = *reinterpret_cast<const T2*>(&cf.w[2 + h]);
+    } else {
+      A[h] = T2{T(cf.w[h].x, cf.w[h].y), T(cf.w[h].z, cf.w[h].w)};
+      B[h] = T2{T(cf.w[2 + h].x, cf.w[2 + h].y), T(cf.w[2 + h].z, cf.w[2 + h].w)};
+    }
+  }
+}
 
 // Geometry of one lane of a segment tile: which of its rows exist, which are
 // Dirichlet, where its column starts.
@@ -326,14 +362,12 @@ __device__ __forceinline__ void warp_tile_march(const LaneGeo<NY>& lg, const Sim
       T2 G[NF][2];
 #pragma unroll
       for (int r = 0; r < NF; ++r) {
-        const auto cf = src.coef_row(t, r);
-        const T2 rc = V::make(cf.x, cf.x), kc = V::make(cf.y, cf.y);
+        T2 A[2], B[2];
+        march_coeffs<T>(src.coef_row(t, r), AM, AK, BM, BK, A, B);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const T2 A = V::fma(kc, AK[h], V::mul(rc, AM[h]));
-          const T2 B = V::fma(kc, BK[h], V::mul(rc, BM[h]));
-          G[r][h] = V::fma(B, F[r][h], V::fma(A, Fp[r][h], Tp[r][h]));
-          Tp[r][h] = V::fma(A, F[r][h], V::mul(B, Fp[r][h]));
+          G[r][h] = V::fma(B[h], F[r][h], V::fma(A[h], Fp[r][h], Tp[r][h]));
+          Tp[r][h] = V::fma(A[h], F[r][h], V::mul(B[h], Fp[r][h]));
         }
       }
       src.after_elements(lg, t, tzl);

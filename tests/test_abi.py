@@ -87,7 +87,7 @@ def test_tuning_table_host_logic(lib):
         api.heat_tuning_variant(n)
     old = api.heat_tuning_get()
     assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512], "pw_quads": [2, 4, 4],
-                   "open_w": [0, 0, 0]}
+                   "open_w": [2, 2, 2]}
     try:
         api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4], [1, 0, 1])
         assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],

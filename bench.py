@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--slab-only", action="store_true", help="run only the z-slab leg")
     ap.add_argument("--serve-only", action="store_true", help="run only the two serving streams")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning table")
+    ap.add_argument("--persistent-compare", type=int, default=1,
+                    help="1: time the persistent inner iteration against the tick graph (headline and batch)")
     ap.add_argument("--tuning-json", default="",
                     help='set the kernel tuning table instead of autotuning, e.g. '
                          '\'{"variant": [-1, 1, 0], "seg_nodes": [2048, 1024, 512]}\'')
@@ -466,6 +468,11 @@ def run_reference(args, world, rank):
 
 # ---------------------------------------------------------------- batch / serving
 
+def set_table(hg, t):
+    """Set the kernel tuning table from a dict (keys missing from it keep their current values)."""
+    hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"), t.get("open_w"), t.get("loop"))
+
+
 def autotune(hg, p, precision, stream, reps=40):
     """Tune the kernel table for this problem's size bucket and precision
     (untimed; CG iterations through the tick graph, as the solve runs them)."""
@@ -473,6 +480,79 @@ def autotune(hg, p, precision, stream, reps=40):
         s.step(1)
         table, ms = hg.heat_autotune(s.sim, reps)
     return {"table": table, "best_ms_per_cg_iteration": ms}
+
+
+def run_persistent(hg, torch, stream, headline_table, batch_table, nsteps_single=30, nsims=256, nsteps_batch=10):
+    """The persistent inner iteration (tuning loop = 1: one cooperative kernel
+    per tick that runs the iterations with a grid barrier after each phase)
+    against the replayed tick graph (an apply and an update launch per
+    iteration), each under its own table, on the first steps of the headline
+    workload and of the batched one. Same work items, so with equal item sizes
+    the fields are bitwise equal (checked here on the headline)."""
+    import workloads as W
+    base = hg.heat_tuning_get()
+    pid = hg.PRECISIONS["fp32_refined"]
+
+    def table(t, loop, quads=None):
+        t = {k: list(v) for k, v in t.items()}
+        t["loop"][pid] = loop
+        if quads is not None:
+            t["pw_quads"][pid] = quads
+        return t
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e), r
+
+    out = {"single": {"workload": f"inclusions_cube_100, first {nsteps_single} steps, fp32_refined"},
+           "batch": {"workload": f"{nsims} x lognormal_cube_40, first {nsteps_batch} steps, fp32_refined"},
+           # one grid barrier alone, 128-thread blocks (the loop runs 3 per SM)
+           "us_per_grid_barrier": {f"{bps}_blocks_per_sm": hg.heat_probe_grid_barrier(bps, 2000) for bps in (1, 3)}}
+    try:
+        p = W.inclusions_cube(nsteps=nsteps_single)
+        fields = {}
+        for name, t in (("tick", table(headline_table, 0)),
+                        ("loop_same_items", table(headline_table, 1)),
+                        ("loop_pw1", table(headline_table, 1, 1)), ("loop_pw2", table(headline_table, 1, 2))):
+            set_table(hg, t)
+            with hg.Simulation.from_problem(p, precision="fp32_refined", stream=stream.cuda_stream) as s:
+                s.step(1)
+                hg.heat_set_state(s.sim, p.u0, s.n_nodes)
+                ms, st = timed(lambda: s.step(nsteps_single))
+                fields[name] = s.state()
+            out["single"][name] = {"ms_per_step": ms / nsteps_single, "cg_iterations": st["iters"],
+                                   "us_per_cg_iteration_incl_step_passes": ms * 1e3 / st["iters"],
+                                   "kernel_launches": st["kernel_launches"], "pw_quads": t["pw_quads"][pid]}
+        out["single"]["loop_bitwise_equal_to_tick"] = bool(np.array_equal(fields["tick"],
+                                                                           fields["loop_same_items"]))
+        ps = [W.lognormal_cube(k, n=40, nsteps=nsteps_batch) for k in range(nsims)]
+        for name, t in (("tick", table(batch_table, 0)), ("loop_pw1", table(batch_table, 1, 1)),
+                        ("loop_pw2", table(batch_table, 1, 2))):
+            set_table(hg, t)
+            sims = [hg.Simulation.from_problem(q, precision="fp32_refined", stream=stream.cuda_stream) for q in ps]
+            b = hg.heat_batch_create([x.sim for x in sims], stream.cuda_stream)
+            try:
+                hg.heat_batch_step(b, 1, nsims)
+                for x, q in zip(sims, ps):
+                    hg.heat_set_state(x.sim, q.u0, x.n_nodes)
+                ms, (rc, stats) = timed(lambda: hg.heat_batch_step(b, nsteps_batch, nsims))
+                its = sum(st["iters"] for st in stats)
+                out["batch"][name] = {"ms_per_step": ms / nsteps_batch, "cg_iterations": its, "rc": rc,
+                                      "kernel_launches": stats[0]["kernel_launches"],
+                                      "dof_cg_iters_per_s": sims[0].n_nodes * its / (ms * 1e-3)}
+            finally:
+                hg.heat_destroy_batch(b)
+                for x in sims:
+                    x.close()
+    finally:
+        set_table(hg, base)
+    return out
 
 
 def run_batch(hg, torch, nsims: int, nsteps: int, stream, tune=True, fixed_tuning=False):
@@ -581,7 +661,7 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
         # Chebyshev-Jacobi against the FP32-refined Jacobi leg, same steps and
         # kernel table (a fused variant gives way to its register-prefetch form)
         if tuned32 is not None:
-            hg.heat_tuning_set(tuned32["table"]["variant"], tuned32["table"]["seg_nodes"], tuned32["table"]["pw_quads"])
+            set_table(hg, tuned32["table"])
         jac = out["fp32_refined"]
         legs = {}
         for m in cheb_degrees:
@@ -610,7 +690,7 @@ def run_layered(hg, torch, nsteps: int, stream, tune=True, cheb_degrees=(), cheb
     pp = W.layered_cube(nsteps=nsteps)
     pp.element = "p1"
     if tuned32 is not None:
-        hg.heat_tuning_set(tuned32["table"]["variant"], tuned32["table"]["seg_nodes"], tuned32["table"]["pw_quads"])
+        set_table(hg, tuned32["table"])
     with hg.Simulation.from_problem(pp, precision="fp32_refined", stream=stream.cuda_stream) as s:
         s.step(1)
         hg.heat_set_state(s.sim, pp.u0, s.n_nodes)
@@ -642,7 +722,7 @@ def run_p1(hg, torch, nsteps: int, stream, table=None):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     peak, _ = measured_peaks()
     if table is not None:  # the headline's kernel table (later legs retune for their own sizes)
-        hg.heat_tuning_set(table["variant"], table["seg_nodes"], table["pw_quads"])
+        set_table(hg, table)
     out["kernel_table"] = hg.heat_tuning_get()
     for element in ("p1", "q1"):
         p = W.inclusions_cube(nsteps=nsteps)
@@ -830,7 +910,7 @@ def main():
     if args.layered_only:  # the 200^3 layered legs alone (used for profiling captures)
         if args.tuning_json:
             t = json.loads(args.tuning_json)
-            hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
+            set_table(hg, t)
         print(json.dumps({"layered": run_layered(hg, torch, args.layered_steps, stream,
                                                  not (args.no_autotune or args.tuning_json),
                                                  cheb_degrees(args), args.cheb_ratio)}), flush=True)
@@ -852,7 +932,7 @@ def main():
         fixed = bool(args.tuning_json)
         if fixed:
             t = json.loads(args.tuning_json)
-            hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
+            set_table(hg, t)
         print(json.dumps({"batched": run_batch(hg, torch, args.batch_sims, args.batch_steps, stream,
                                                not args.no_autotune, fixed)}), flush=True)
         return
@@ -861,7 +941,7 @@ def main():
     fixed = bool(args.tuning_json)
     if fixed:
         t = json.loads(args.tuning_json)
-        hg.heat_tuning_set(t["variant"], t["seg_nodes"], t.get("pw_quads"))
+        set_table(hg, t)
         tuning = {"table": hg.heat_tuning_get(), "set_by": "--tuning-json"}
     else:
         tuning = None if args.no_autotune else autotune(hg, p, args.precision, stream)
@@ -952,6 +1032,11 @@ def main():
     batched = serving = layered = mh = p1 = None
     if rank == 0 and args.batch_sims > 0:
         batched = run_batch(hg, torch, args.batch_sims, args.batch_steps, stream, not args.no_autotune, fixed)
+    persistent = None
+    if rank == 0 and args.persistent_compare:
+        bt = (batched or {}).get("tuning") or {}
+        persistent = run_persistent(hg, torch, stream, tuning["table"] if tuning else hg.heat_tuning_get(),
+                                    bt.get("table") or hg.heat_tuning_get())
     if rank == 0 and args.layered_steps > 0:
         layered = run_layered(hg, torch, args.layered_steps, stream, not (args.no_autotune or fixed),
                               cheb_degrees(args), args.cheb_ratio)
@@ -994,6 +1079,7 @@ def main():
             "fp64_path": fp64,
             "final_field_rel_err_vs_fp64_path": final_err,
             "batched": batched,
+            "persistent_iteration": persistent,
             "layered": layered,
             "inverse_problem": mh,
             "tetrahedra": p1,

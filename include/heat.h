@@ -280,6 +280,15 @@ void heat_destroy_server(heat_server* srv);
  * that status and the requests already running continue undisturbed. n = 0
  * clears the hook. */
 heat_status heat_debug_fail_engine_builds(int n);
+/* Testing hook for the bounded waits of the persistent iteration (tuning
+ * loop): engines built or refreshed afterwards expect extra_arrivals (0 or 1)
+ * arrivals at each grid barrier beyond their grid, so with 1 no barrier ever
+ * completes, and bound one wait by limit_s seconds (0: the engine's own
+ * bound of 1 s plus 50 ns per node). A wait that runs out ends the kernel;
+ * the step then fails with HEAT_ERR_TIMEOUT and the GPU context stays
+ * usable. HEAT_ERR_ARG unless extra_arrivals is 0 or 1 and
+ * 0 <= limit_s <= 60. heat_debug_loop_wait(0, 0) restores the defaults. */
+heat_status heat_debug_loop_wait(unsigned int extra_arrivals, double limit_s);
 
 /* ---- operator-level entry points (device pointers, sim stream) ---------- */
 
@@ -510,6 +519,12 @@ heat_status heat_batch_profile_iteration(heat_batch* batch, int reps, void* flus
  * FP64 operator passes are measured against: on this GPU FP64 arithmetic,
  * not memory traffic, bounds them (§5.1 runs the paper's kernels in FP64). */
 heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops);
+/* Microseconds one grid barrier of the persistent iteration (tuning loop)
+ * takes on its own: a cooperative launch of blocks_per_sm 128-thread blocks
+ * per SM passes `reps` barriers (best of three launches). Every wait is
+ * bounded by 1 s (HEAT_ERR_TIMEOUT if one runs out). HEAT_ERR_ARG unless
+ * 1 <= blocks_per_sm <= the blocks that fit an SM and 1 <= reps <= 100000. */
+heat_status heat_probe_grid_barrier(int blocks_per_sm, int reps, double* us_per_barrier);
 
 /* ---- kernel tuning ------------------------------------------------------ */
 
@@ -532,12 +547,23 @@ heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops);
  *     warp-segment march with two-row segments, 2 with one-row segments
  *     (default {2, 2, 2}; trilinear boxes only, six-tetrahedra boxes always
  *     use block tiles). On trilinear boxes the passes of the A operator read
- *     each element's precomputed Walsh-pair coefficients. */
+ *     each element's precomputed Walsh-pair coefficients.
+ *   loop[p]: for heat_precision p, how the CG iterations of a tick run:
+ *     0 as an apply launch and an update launch per iteration, 1 as ONE
+ *     persistent cooperative kernel that runs the same work items with a
+ *     grid barrier after each phase, until no simulation of the engine is
+ *     still iterating or 256 iterations (results bitwise the same; every
+ *     barrier wait is bounded, and a wait that runs out fails the
+ *     unfinished simulations with HEAT_ERR_TIMEOUT). Only for the FP32
+ *     paths (loop[HEAT_FP64] must be 0) with a register-prefetch variant
+ *     (stages 0, not fused) on trilinear boxes without Chebyshev passes;
+ *     elsewhere the flag is ignored. Default {0, 0, 0}. */
 typedef struct heat_tuning {
   int variant[3];
   int seg_nodes[3];
   int pw_quads[3];
   int open_w[3];
+  int loop[3];
 } heat_tuning;
 int heat_tuning_num_variants(void);
 /* Shape of variant v: segment width in nodes along x (one lane per node),

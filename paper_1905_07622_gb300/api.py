@@ -86,11 +86,11 @@ class heat_mh_config(C.Structure):
 
 class heat_tuning(C.Structure):
     _fields_ = [("variant", C.c_int * 3), ("seg_nodes", C.c_int * 3), ("pw_quads", C.c_int * 3),
-                ("open_w", C.c_int * 3)]
+                ("open_w", C.c_int * 3), ("loop", C.c_int * 3)]
 
     def as_dict(self):
         return {"variant": list(self.variant), "seg_nodes": list(self.seg_nodes), "pw_quads": list(self.pw_quads),
-                "open_w": list(self.open_w)}
+                "open_w": list(self.open_w), "loop": list(self.loop)}
 
 
 class heat_server_stats(C.Structure):
@@ -172,6 +172,8 @@ _SIGS = [
     ("heat_destroy_slab", None, [_VP]),
     ("heat_probe_fma_rate", C.c_int, [C.c_int, C.c_int, _DP]),
     ("heat_debug_fail_engine_builds", C.c_int, [C.c_int]),
+    ("heat_debug_loop_wait", C.c_int, [C.c_uint, C.c_double]),
+    ("heat_probe_grid_barrier", C.c_int, [C.c_int, C.c_int, _DP]),
     ("heat_checks_compiled", C.c_int, []),
     ("heat_check_violations", C.c_int, [_VP, C.POINTER(C.c_uint)]),
     ("heat_last_error", C.c_char_p, []),
@@ -540,6 +542,22 @@ def heat_debug_fail_engine_builds(n: int):
     _check(_lib.heat_debug_fail_engine_builds(int(n)))
 
 
+def heat_debug_loop_wait(extra_arrivals: int, limit_s: float):
+    """Testing hook: engines built afterwards expect extra_arrivals (0 or 1) more
+    arrivals at each persistent-iteration barrier and bound one wait by
+    limit_s seconds (0: the default bound)."""
+    load_library()
+    _check(_lib.heat_debug_loop_wait(int(extra_arrivals), float(limit_s)))
+
+
+def heat_probe_grid_barrier(blocks_per_sm: int, reps: int = 2000) -> float:
+    """Microseconds per grid barrier of the persistent iteration, measured alone."""
+    load_library()
+    us = C.c_double()
+    _check(_lib.heat_probe_grid_barrier(int(blocks_per_sm), int(reps), C.byref(us)))
+    return us.value
+
+
 def heat_probe_fma_rate(fp64: bool, reps: int = 5) -> float:
     """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
     load_library()
@@ -568,17 +586,19 @@ def heat_tuning_get() -> dict:
     return t.as_dict()
 
 
-def heat_tuning_set(variant, seg_nodes, pw_quads=None, open_w=None):
-    """Set the table; pw_quads=None / open_w=None keep the current pointwise
-    item sizes / open-pass forms."""
+def heat_tuning_set(variant, seg_nodes, pw_quads=None, open_w=None, loop=None):
+    """Set the table; pw_quads=None / open_w=None / loop=None keep the current
+    pointwise item sizes / open-pass forms / iteration forms."""
     load_library()
     cur = heat_tuning_get()
     if pw_quads is None:
         pw_quads = cur["pw_quads"]
     if open_w is None:
         open_w = cur["open_w"]
+    if loop is None:
+        loop = cur["loop"]
     t = heat_tuning((C.c_int * 3)(*variant), (C.c_int * 3)(*seg_nodes), (C.c_int * 3)(*pw_quads),
-                    (C.c_int * 3)(*open_w))
+                    (C.c_int * 3)(*open_w), (C.c_int * 3)(*loop))
     _check(_lib.heat_tuning_set(C.byref(t)))
 
 

@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "engine.h"
+#include "loop_kernels.cuh"
 #include "open_kernels.cuh"
 
 namespace heat {
@@ -39,6 +40,9 @@ struct KernelSet {
   // `open` when set), on their own segment geometry and work list
   TileFn open_w = nullptr;
   int owsx = 0, owny = 0, owwarps = 0;
+  // the CG iterations of a tick as one persistent kernel (replaces the
+  // apply and update launches when set; FP32 paths, register-prefetch apply)
+  LoopFn loop = nullptr;
 };
 
 // The warp-segment forms of k_open (tuning open_w): 32-lane segments of 2
@@ -135,7 +139,7 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // variant per precision (-1: the block-tile apply) and the segment tile size
 // per mesh-size bucket. Both are fixed per simulation size, so results stay
 // bitwise identical alone and in batches built under the same table.
-static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}, {2, 2, 2}};
+static Tuning g_tuning = {{-1, 0, 0}, {512, 512, 512}, {2, 4, 4}, {2, 2, 2}, {0, 0, 0}};
 static std::mutex g_tuning_mu;
 
 int num_variants() { return kNumVariants; }
@@ -170,6 +174,9 @@ heat_status tuning_set(const Tuning& t) {
   for (int p = 0; p < 3; ++p)
     if (t.open_w[p] < 0 || t.open_w[p] > 2)
       return set_error(HEAT_ERR_ARG, "tuning: open_w[%d] = %d not 0, 1 or 2", p, t.open_w[p]);
+  for (int p = 0; p < 3; ++p)
+    if (t.loop[p] < 0 || t.loop[p] > 1 || (p == P_FP64 && t.loop[p] != 0))
+      return set_error(HEAT_ERR_ARG, "tuning: loop[%d] = %d not 0 or 1 (0 for FP64)", p, t.loop[p]);
   for (int b = 0; b < 3; ++b)
     if (t.seg_nodes[b] < 32 || t.seg_nodes[b] > (1 << 20))
       return set_error(HEAT_ERR_ARG, "tuning: segment size %d out of range", t.seg_nodes[b]);
@@ -226,6 +233,10 @@ static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int el
       k.cheb_w = prec == P_FP64 ? v.cheb64[ei] : v.cheb32[ei];
       if (k.apply_w_smem > 0)
         cudaFuncSetAttribute(k.apply_w, cudaFuncAttributeMaxDynamicSharedMemorySize, k.apply_w_smem);
+      // the persistent iteration: FP32 paths, trilinear boxes, register
+      // prefetch, separate update, no Chebyshev passes
+      if (t.loop[prec] && prec != P_FP64 && elem == E_Q1 && !cheb && !v.fused && v.stages == 0)
+        k.loop = loop_kernel(v.sx, v.ny, v.warps, t.pw_quads[prec]);
     }
   }
   if (elem == E_Q1 && t.open_w[prec]) {
@@ -287,6 +298,10 @@ struct Engine {
   int grid_ch = 0;  // grid of the pass kernel
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // persistent iteration (ks.loop): its barrier state and grid
+  GridSync* d_sync = nullptr;
+  int* h_abort = nullptr;
+  int grid_loop = 0;
   long long launches = 0;  // kernels launched by the last engine_step_all
   int* d_phases = nullptr;
   int* h_phases = nullptr;
@@ -308,17 +323,65 @@ static bool injected_failure() {
 }
 
 // Kernels in one tick: k_open, then per iteration the Chebyshev passes and
-// apply + update, or the fused kernel.
+// apply + update, or the fused kernel; or k_open and the persistent loop.
 static int tick_launches(const Engine* e) {
+  if (e->ks.loop) return 2;
   return 1 + (e->ncheb + (e->ks.fused ? 1 : 2)) * e->iters_per_tick;
 }
 
+// Rounds (CG iterations) one persistent launch runs at most: a solve's
+// inner iterations normally end it first, at a phase change.
+constexpr int kLoopRounds = 256;
+
+// Test hook (heat_debug_loop_wait): arrivals the barrier expects beyond the
+// grid, and the bound of one wait in ns (0: the engine's own bound).
+static std::atomic<unsigned int> g_loop_extra{0};
+static std::atomic<unsigned long long> g_loop_limit_ns{0};
+
+// Barrier state for a fresh launch. One wait is bounded by 1 s plus 50 ns
+// per node of the members (a phase of the largest batches takes far less),
+// or by the test hook's bound; a launch runs at most `rounds` iterations.
+static heat_status loop_sync_reset(Engine* e, int rounds = kLoopRounds) {
+  if (!e->d_sync) return HEAT_OK;
+  long long nodes = 0;
+  for (const heat_sim* s : e->sims) nodes += s->nn;
+  GridSync g{};
+  g.extra = g_loop_extra.load();
+  const unsigned long long hook = g_loop_limit_ns.load();
+  g.limit_ns = hook ? hook : 1000000000ull + 50ull * (unsigned long long)nodes;
+  g.rounds = rounds;
+  CUDA_TRY(cudaMemcpyAsync(e->d_sync, &g, sizeof(g), cudaMemcpyHostToDevice, e->stream));
+  CUDA_TRY(cudaStreamSynchronize(e->stream));
+  return HEAT_OK;
+}
+
+// After a persistent launch gave up waiting (GridSync::abort): the members'
+// iteration state is incomplete, so every member that has not finished
+// fails with HEAT_ERR_TIMEOUT, and the barrier state is reset.
+static heat_status loop_abort(Engine* e) {
+  for (heat_sim* s : e->sims) {
+    heat_status st = sim_read_scalars(s);
+    if (st != HEAT_OK) return st;
+    SimScalars* sc = s->h_sc;
+    if (sc->phase != PH_DONE && sc->phase != PH_FAILED && sc->phase != PH_IDLE) {
+      sc->status = HEAT_ERR_TIMEOUT;
+      sc->phase = PH_FAILED;
+    }
+    sc->count = 0;
+    st = sim_write_scalars(s);
+    if (st != HEAT_OK) return st;
+  }
+  *e->h_abort = 0;
+  return loop_sync_reset(e);
+}
+
 // Chebyshev passes the members need per iteration.
-static int members_ncheb(const Engine* e) {
+static int members_ncheb_of(heat_sim* const* sims, int nsims) {
   int n = 0;
-  for (const heat_sim* s : e->sims) n = std::max(n, s->dev.cheb_m >= 2 ? s->dev.cheb_m - 1 : 0);
+  for (int i = 0; i < nsims; ++i) n = std::max(n, sims[i]->dev.cheb_m >= 2 ? sims[i]->dev.cheb_m - 1 : 0);
   return n;
 }
+static int members_ncheb(const Engine* e) { return members_ncheb_of(e->sims.data(), (int)e->sims.size()); }
 
 // Operator tile geometry of one simulation: (SX-1) x (SY-1) node columns per
 // tile, tz_len levels. tz_len trades z-halo work (3 extra levels per tile)
@@ -426,6 +489,13 @@ static heat_status engine_upload(Engine* e) {
   int occ_ow = 1;
   if (e->ks.open_w)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ow, e->ks.open_w, 32 * e->ks.owwarps, 0);
+  if (e->ks.loop) {
+    // every block resident at once (the launch is cooperative)
+    int occ_loop = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_loop, (const void*)e->ks.loop, 32 * e->ks.wwarps, 0);
+    if (occ_loop < 1) return set_error(HEAT_ERR_CUDA, "engine: the persistent iteration kernel does not fit an SM");
+    e->grid_loop = sms * occ_loop;
+  }
   // With grid_cap the grids cover the capacities, so a later member set that
   // fits them runs under the same captured graph (surplus blocks find no item).
   const long long items[4] = {e->grid_cap ? e->cap_op : nwork[0], e->grid_cap ? e->cap_pw : nwork[1],
@@ -498,7 +568,23 @@ static heat_status engine_capture(Engine* e) {
     cudaError_t lerr = e->ks.open_w
                            ? launch(e->ks.open_w, e->grid_ow, 32 * e->ks.owwarps, e->d_work_ow, e->d_nwork + 3, 0)
                            : launch(e->ks.open, e->grid_op, e->ks.open_threads, e->d_work_op, e->d_nwork, 0);
-    for (int it = 0; it < e->iters_per_tick && lerr == cudaSuccess; ++it) {
+    if (e->ks.loop && lerr == cudaSuccess) {
+      // one persistent launch for the tick's iterations: cooperative (all
+      // blocks resident, which its grid barriers need), no early start
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(e->grid_loop);
+      cfg.blockDim = dim3(32 * e->ks.wwarps);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = cap;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      lerr = cudaLaunchKernelEx(&cfg, e->ks.loop, (const SimDev*)e->d_sims, (const int2*)e->d_work_aw,
+                                (const int2*)e->d_work_pw, (const int*)e->d_nwork, e->d_sync);
+    }
+    for (int it = 0; it < (e->ks.loop ? 0 : e->iters_per_tick) && lerr == cudaSuccess; ++it) {
       for (int k = 0; k < e->ncheb && lerr == cudaSuccess; ++k) {
         if (e->ks.cheb_w) lerr = launch(e->ks.cheb_w, e->grid_ch, 32 * e->ks.wwarps, e->d_work_aw, e->d_nwork + 2, 0);
         else lerr = launch(e->ks.cheb, e->grid_ch, e->ks.apply_threads, e->d_work_op, e->d_nwork, 0);
@@ -579,7 +665,9 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
       cudaMalloc(&e->d_nwork, sizeof(int) * 4) != cudaSuccess ||
       cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_partial, sizeof(double) * 4 * cap_partial) != cudaSuccess ||
-      cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_sync, sizeof(GridSync)) != cudaSuccess ||
+      cudaMallocHost(&e->h_abort, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_error(HEAT_ERR_NOMEM, "engine: device allocation failed"));
   }
@@ -592,6 +680,9 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
     if (st != HEAT_OK) return fail(st);
   }
   st = engine_upload(e);
+  if (st != HEAT_OK) return fail(st);
+  *e->h_abort = 0;
+  st = loop_sync_reset(e);
   if (st != HEAT_OK) return fail(st);
   st = engine_capture(e);
   if (st != HEAT_OK) return fail(st);
@@ -612,6 +703,8 @@ void engine_destroy(Engine* e) {
   cudaFree(e->d_nwork);
   cudaFree(e->d_unfinished);
   cudaFree(e->d_partial);
+  if (e->d_sync) cudaFree(e->d_sync);
+  if (e->h_abort) cudaFreeHost(e->h_abort);
   if (e->h_unfinished) cudaFreeHost(e->h_unfinished);
   if (e->d_phases) cudaFree(e->d_phases);
   if (e->h_phases) cudaFreeHost(e->h_phases);
@@ -637,6 +730,8 @@ heat_status engine_refresh(Engine* e) {
   }
   e->ncheb = nch;
   heat_status st = engine_upload(e);
+  if (st != HEAT_OK) return st;
+  st = loop_sync_reset(e);
   if (st != HEAT_OK) return st;
   if (recapture || !e->gexec || e->grid_op != g_op || e->grid_pw != g_pw || e->grid_aw != g_aw || e->grid_ch != g_ch)
     return engine_capture(e);
@@ -677,6 +772,10 @@ heat_status engine_set_members(Engine* e, heat_sim* const* sims, int nsims) {
 
 heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int reset_counters) {
   int max_iter = 1, max_outer = 1, poll = 32;
+  if (e->ks.loop) {  // the barrier bound and the test hook as they are now
+    heat_status st = loop_sync_reset(e);
+    if (st != HEAT_OK) return st;
+  }
   for (heat_sim* s : e->sims) {
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     heat_status st = sim_read_scalars(s);
@@ -698,6 +797,7 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
     max_outer = std::max(max_outer, s->prm.max_outer);
     poll = std::min(poll, s->prm.poll_period);
   }
+  // the persistent form polls after as many graph launches as the tick form
   const int ticks_per_poll = std::max(1, poll / e->iters_per_tick);
   // Every tick advances each unfinished simulation by at least one CG
   // iteration or one phase change, so this bound is never reached by a
@@ -712,7 +812,14 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
     k_count_unfinished<<<1, 256, 0, e->stream>>>(e->d_sims, (int)e->sims.size(), e->d_unfinished);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(e->h_unfinished, e->d_unfinished, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    if (e->ks.loop)
+      CUDA_TRY(cudaMemcpyAsync(e->h_abort, &e->d_sync->abort, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (e->ks.loop && *e->h_abort) {
+      heat_status st = loop_abort(e);
+      if (st != HEAT_OK) return st;
+      break;
+    }
     if (*e->h_unfinished == 0) break;
     if (ticks > max_ticks) return set_error(HEAT_ERR_TIMEOUT, "engine: solve did not finish within %lld ticks", ticks);
   }
@@ -767,6 +874,14 @@ heat_status engine_read_phases(Engine* e, int* phases) {
     e->phases_cap = n;
   }
   d = e->d_phases;
+  if (e->ks.loop) {  // a persistent launch that gave up fails the unfinished members first
+    CUDA_TRY(cudaMemcpyAsync(e->h_abort, &e->d_sync->abort, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (*e->h_abort) {
+      heat_status st = loop_abort(e);
+      if (st != HEAT_OK) return st;
+    }
+  }
   k_gather_phases<<<(n + 255) / 256, 256, 0, e->stream>>>(e->d_sims, n, d);
   CUDA_TRY(cudaGetLastError());
   e->launches += 1;
@@ -873,6 +988,13 @@ static heat_status profile_arm(Engine* e, double* d_delta, std::vector<double>& 
 }
 
 static heat_status profile_check(Engine* e) {
+  if (e->ks.loop) {
+    CUDA_TRY(cudaMemcpy(e->h_abort, &e->d_sync->abort, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*e->h_abort) {
+      heat_status st = loop_abort(e);
+      return st != HEAT_OK ? st : set_error(HEAT_ERR_TIMEOUT, "profile: a persistent iteration's wait ran out");
+    }
+  }
   for (heat_sim* s : e->sims) {
     heat_status st = sim_read_scalars(s);
     if (st != HEAT_OK) return st;
@@ -973,7 +1095,15 @@ heat_status prime_products(heat_sim* s, int nslots) {
 }
 
 heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
-  const int chunk_ticks = std::max(1, 40 / e->iters_per_tick);  // below the inner cap
+  // 40 iterations per timed chunk: below the inner cap, and on small meshes
+  // short of the point where a seeded residual has converged to rounding
+  constexpr int kChunk = 40;
+  const int per_tick = e->ks.loop ? kChunk : e->iters_per_tick;
+  const int chunk_ticks = e->ks.loop ? 1 : std::max(1, kChunk / e->iters_per_tick);
+  if (e->ks.loop) {
+    heat_status st = loop_sync_reset(e, kChunk);
+    if (st != HEAT_OK) return st;
+  }
   cudaEvent_t a, b;
   CUDA_TRY(cudaEventCreate(&a));
   if (cudaEventCreate(&b) != cudaSuccess) {
@@ -990,7 +1120,7 @@ heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
   double ms = 0.0;
   long long iters = 0;
   for (int done = 0; done < reps && st == HEAT_OK;) {
-    const int ticks = std::min(chunk_ticks, std::max(1, (reps - done + e->iters_per_tick - 1) / e->iters_per_tick));
+    const int ticks = std::min(chunk_ticks, std::max(1, (reps - done + per_tick - 1) / per_tick));
     st = profile_arm(e, d_delta, h_delta);
     if (st != HEAT_OK) break;
     cudaEventRecord(a, e->stream);
@@ -1002,13 +1132,20 @@ heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
     float t = 0.f;
     cudaEventElapsedTime(&t, a, b);
     ms += t;
-    iters += (long long)ticks * e->iters_per_tick;
-    done += ticks * e->iters_per_tick;
     st = profile_check(e);
+    if (st != HEAT_OK) break;
+    // iterations actually run (profile_arm cleared iter_step; every member iterates alike)
+    const long long n = e->sims[0]->h_sc->iter_step;
+    iters += n;
+    done += (int)std::max(1LL, n);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(d_delta);
+  if (e->ks.loop) {
+    const heat_status st2 = loop_sync_reset(e);
+    if (st == HEAT_OK) st = st2;
+  }
   if (st != HEAT_OK) return st;
   *ms_per_iter = ms / (double)std::max(1LL, iters);
   return HEAT_OK;
@@ -1061,6 +1198,27 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
       best = t;
     }
   }
+  // then the persistent iteration with each item size (FP32 paths, where
+  // the chosen apply has a persistent form)
+  const Tuning chosen2 = best;
+  for (int qpt : {1, 2, 4}) {
+    if (st != HEAT_OK || prec == P_FP64) break;
+    Tuning t = chosen2;
+    t.loop[prec] = 1;
+    t.pw_quads[prec] = qpt;
+    if (!kernel_set(prec, t, members_ncheb_of(sims, nsims) > 0, sims[0]->dev.elem).loop) continue;
+    Engine* e = nullptr;
+    st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
+    if (st != HEAT_OK) break;
+    double ms = 0.0;
+    st = engine_time_iterations(e, 8, &ms);
+    if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
+    engine_destroy(e);
+    if (st == HEAT_OK && ms < best_t) {
+      best_t = ms;
+      best = t;
+    }
+  }
   if (st != HEAT_OK) return st;
   st = tuning_set(best);
   if (st != HEAT_OK) return st;
@@ -1071,6 +1229,14 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
 }
 
 }  // namespace heat
+
+extern "C" heat_status heat_debug_loop_wait(unsigned int extra_arrivals, double limit_s) {
+  if (extra_arrivals > 1u || !(limit_s >= 0.0) || limit_s > 60.0)
+    return heat::set_error(HEAT_ERR_ARG, "heat_debug_loop_wait: need extra_arrivals in {0, 1}, 0 <= limit_s <= 60");
+  heat::g_loop_extra.store(extra_arrivals);
+  heat::g_loop_limit_ns.store((unsigned long long)(limit_s * 1e9));
+  return HEAT_OK;
+}
 
 extern "C" heat_status heat_debug_fail_engine_builds(int n) {
   if (n < 0) return heat::set_error(HEAT_ERR_ARG, "heat_debug_fail_engine_builds: n must be >= 0");

@@ -15,6 +15,13 @@ struct heat_mesh {
 
 namespace heat {
 struct Engine;
+struct GridSync;
+// The persistent inner iteration (loop_kernels.cuh): sims, apply and update
+// work lists, their counts, the grid barrier state (with the round limit).
+using LoopFn = void (*)(const SimDev*, const int2*, const int2*, const int*, GridSync*);
+// Its instance for a register-prefetch warp-apply shape (segment width, rows,
+// warps) and pointwise item size (groups per thread); nullptr if none.
+LoopFn loop_kernel(int sx, int ny, int warps, int qpt);
 }
 
 struct heat_sim {
@@ -71,6 +78,7 @@ struct Tuning {
   int seg_nodes[3];
   int pw_quads[3];  // k_update: groups of 4 nodes per thread (1, 2 or 4), per precision
   int open_w[3];    // per precision: 1 runs k_open's passes in the warp-segment march (k_open_w)
+  int loop[3];      // per precision: 1 runs a tick's CG iterations as one persistent kernel (k_cg_loop)
 };
 int size_bucket(long long nn);
 int num_variants();

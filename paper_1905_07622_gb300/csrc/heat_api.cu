@@ -848,6 +848,7 @@ extern "C" heat_status heat_tuning_get(heat_tuning* t) {
     t->seg_nodes[i] = x.seg_nodes[i];
     t->pw_quads[i] = x.pw_quads[i];
     t->open_w[i] = x.open_w[i];
+    t->loop[i] = x.loop[i];
   }
   return HEAT_OK;
 }
@@ -860,6 +861,7 @@ extern "C" heat_status heat_tuning_set(const heat_tuning* t) {
     x.seg_nodes[i] = t->seg_nodes[i];
     x.pw_quads[i] = t->pw_quads[i];
     x.open_w[i] = t->open_w[i];
+    x.loop[i] = t->loop[i];
   }
   return tuning_set(x);
 }

@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "engine.h"
+#include "loop_kernels.cuh"
 
 namespace {
 
@@ -69,7 +70,80 @@ heat_status probe(int reps, double* tflops) {
   return rc;
 }
 
+// reps grid barriers of the persistent iteration (grid_barrier), nothing else
+__global__ void __launch_bounds__(128) k_barrier_rate(heat::GridSync* gs, int reps, int* passed) {
+  bool any = false;
+  int ok = 1;
+  for (int r = 0; r < reps && ok; ++r) ok = heat::grid_barrier(gs, gridDim.x, false, any) ? 1 : 0;
+  if (threadIdx.x == 0 && ok) atomicAdd(passed, 1);
+}
+
 }  // namespace
+
+// The cost of one grid barrier of the persistent iteration on its own: a
+// cooperative launch of blocks_per_sm 128-thread blocks per SM runs reps
+// barriers; best of three launches, after one warm-up.
+extern "C" heat_status heat_probe_grid_barrier(int blocks_per_sm, int reps, double* us_per_barrier) {
+  if (!us_per_barrier || blocks_per_sm < 1 || blocks_per_sm > 16 || reps < 1 || reps > 100000)
+    return heat::set_error(HEAT_ERR_ARG, "heat_probe_grid_barrier: need 1 <= blocks_per_sm <= 16, 1 <= reps <= 1e5");
+  int dev = 0, sms = 1, occ = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_barrier_rate, 128, 0));
+  if (blocks_per_sm > occ) return heat::set_error(HEAT_ERR_ARG, "heat_probe_grid_barrier: at most %d blocks per SM", occ);
+  heat::GridSync* gs = nullptr;
+  int* passed = nullptr;
+  CUDA_TRY(cudaMalloc(&gs, sizeof(heat::GridSync)));
+  if (cudaMalloc(&passed, sizeof(int)) != cudaSuccess) {
+    cudaFree(gs);
+    return heat::set_error(HEAT_ERR_NOMEM, "heat_probe_grid_barrier: allocation failed");
+  }
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  heat_status rc = HEAT_OK;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    rc = heat::set_error(HEAT_ERR_CUDA, "heat_probe_grid_barrier: stream or event creation failed");
+  }
+  const unsigned int grid = (unsigned int)(sms * blocks_per_sm);
+  double best = 1e300;
+  for (int t = -1; t < 3 && rc == HEAT_OK; ++t) {  // t = -1: warm-up
+    heat::GridSync g{};
+    g.limit_ns = 1000000000ull;  // 1 s per wait
+    int zero = 0;
+    if (cudaMemcpyAsync(gs, &g, sizeof(g), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(passed, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = heat::set_error(HEAT_ERR_CUDA, "heat_probe_grid_barrier: upload failed");
+      break;
+    }
+    void* args[] = {&gs, &reps, &passed};
+    cudaEventRecord(a, st);
+    const cudaError_t le = cudaLaunchCooperativeKernel((const void*)k_barrier_rate, dim3(grid), dim3(128), args, 0, st);
+    cudaEventRecord(b, st);
+    int got = 0;
+    if (le != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaMemcpy(&got, passed, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      rc = heat::set_error(HEAT_ERR_CUDA, "heat_probe_grid_barrier: launch failed");
+      break;
+    }
+    if (got != (int)grid) {
+      rc = heat::set_error(HEAT_ERR_TIMEOUT, "heat_probe_grid_barrier: a barrier wait ran out");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (t >= 0) best = std::min(best, (double)ms * 1e3 / reps);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(gs);
+  cudaFree(passed);
+  if (rc == HEAT_OK) *us_per_barrier = best;
+  return rc;
+}
 
 extern "C" heat_status heat_probe_fma_rate(int fp64, int reps, double* tflops) {
   if (!tflops || reps < 1 || (fp64 != 0 && fp64 != 1))

@@ -110,13 +110,17 @@ __device__ __forceinline__ void allow_next_launch() { cudaTriggerProgrammaticLau
 // sums are converted to FP64 and added by thread 0 in warp order. (On this
 // GPU FP64 runs at 1/58 of the FP32 rate, so FP64 work per thread would cost
 // more than the streaming it accompanies.) red: NV*32 doubles. Result in thread 0.
-template <class T, int NV>
-__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV], double* red) {
+//
+// VT > 1: each thread stands for VT threads of a block VT times larger
+// (virtual thread tid + u * blockDim.x holds v[u]); the sum is then bitwise
+// the one that larger block would form: virtual warp k = warp + u * nwarps.
+template <class T, int NV, int VT = 1>
+__device__ __forceinline__ void block_sum_t(const T (&v)[VT * NV], double (&out)[NV], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
-  T w[NV];
+  T w[VT * NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) {
+  for (int a = 0; a < VT * NV; ++a) {
     w[a] = v[a];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w[a] += __shfl_down_sync(0xffffffffu, w[a], o);
@@ -124,14 +128,16 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV],
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) red[a * 32 + warp] = (double)w[a];
+    for (int u = 0; u < VT; ++u)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) red[a * 32 + warp + u * nwarps] = (double)w[u * NV + a];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       double t = 0.0;
-      for (int k = 0; k < nwarps; ++k) t += red[a * 32 + k];
+      for (int k = 0; k < VT * nwarps; ++k) t += red[a * 32 + k];
       out[a] = t;
     }
   }
@@ -142,10 +148,10 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV],
 // simulation's last item of this kernel sums all items' partials (in item
 // order) and returns true, with the totals in lane 0's out. The other warps
 // do not wait for the count.
-template <class T, int NV>
-__device__ __forceinline__ bool finish_item(const SimDev& s, int item, int nitems, const T (&v)[NV],
+template <class T, int NV, int VT = 1>
+__device__ __forceinline__ bool finish_item(const SimDev& s, int item, int nitems, const T (&v)[VT * NV],
                                             double (&out)[NV], double* red) {
-  block_sum_t<T, NV>(v, out, red);
+  block_sum_t<T, NV, VT>(v, out, red);
   if (threadIdx.x >= 32) return false;
   int last = 0;
   if (threadIdx.x == 0) {
@@ -338,6 +344,76 @@ __global__ void __launch_bounds__(SX* SY) k_apply_dot(const SimDev* __restrict__
   }
 }
 
+// Loads of vectors that an earlier phase of the same launch wrote (the
+// persistent iteration kernel, loop_kernels.cuh) go through L2 only (ld.cg):
+// the SM's L1 is not coherent with other SMs' stores. Between kernels L1
+// starts empty, so the separate kernels use plain loads.
+template <bool CG, class T>
+__device__ __forceinline__ T ld_vec(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// One work item of the warp-segment apply (k_apply_dot_w): SPC consecutive
+// segment tiles of one simulation in phase PH_ITER, its partial of d.q and,
+// in the block that finishes the simulation's last item, alpha. CG: r and
+// d_old are loaded through L2 only (see ld_vec).
+template <class T, int SX, int NY, int WARPS, int STAGES, int E, bool CG>
+__device__ __forceinline__ void apply_w_item(const SimDev& s, const Ctl& c, int item, double* red,
+                                             unsigned char* stage_smem) {
+  static_assert(!CG || STAGES == 0, "the L2-only loads exist for the register-prefetch form");
+  constexpr int SPC = WARPS * (32 / SX);  // segments per block
+  const Geo g(s);
+  const int tile = item * SPC + (int)threadIdx.x / SX;
+  const bool active = tile < s.w_ntiles;
+  const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
+  const T* __restrict__ r = s.cheb_m >= 2 ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);  // see k_apply_dot
+  const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+  const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
+  T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
+  T* __restrict__ q = IterVecs<T>::q(s);
+  const bool rs = c.restart != 0;
+  const T beta = rs ? T(0) : (T)c.beta;
+  T acc = T(0);
+  auto out = [&](int m, bool dir, T y, T v) {
+    const T qv = dir ? T(0) : y;
+    q[m] = qv;
+    dnew[m] = v;
+    acc += v * qv;
+  };
+  if constexpr (STAGES == 0) {
+    warp_tile_op_e<E, T, SX, NY>(
+        g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
+        (T)s.theta, true,
+        [&](int m, bool live) -> DirRaw<T> {
+          if (!live) return {T(0), T(0), T(0)};
+          return {pinv[m], ld_vec<CG>(r + m), rs ? T(0) : ld_vec<CG>(dold + m)};
+        },
+        [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
+  } else {
+    using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(IterVecs<T>::coef(s)[0])>::type>::type;
+    const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
+    AsyncSrc<T, NY, STAGES, CoefT> src(pinv, r, rs ? nullptr : dold, IterVecs<T>::coef(s), beta, stage_smem,
+                                       (int)blockDim.x, (int)threadIdx.x, tz * s.w_tz);
+    warp_march_e<E, T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
+  }
+  const T accv[1] = {acc};
+  double tot[1];
+  if (finish_item<T, 1>(s, item, s.w_items, accv, tot, red)) {
+    SimScalars* sc = s.sc;
+    sc->count = 0;
+    const double dq = tot[0];
+    sc->dq = dq;
+    if (!isfinite(dq)) fail(sc, ST_NONFINITE);
+    else if (!(dq > 0.0)) fail(sc, ST_BREAKDOWN);
+    else {
+      sc->alpha = sc->delta / dq;
+      sc->id ^= 1;
+      sc->restart = 0;
+    }
+  }
+}
+
 // Warp-segment version of k_apply_dot (op_warp.cuh): a work item is a group
 // of SPC consecutive segment tiles of one simulation; the level loop has no
 // block barrier. Same results contract as k_apply_dot. STAGES = 0 loads one
@@ -348,7 +424,6 @@ template <class T, int SX, int NY, int WARPS, int STAGES, int MINB, int E = E_Q1
 __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* __restrict__ sims,
                                                             const int2* __restrict__ work,
                                                             const int* __restrict__ nwork_p) {
-  constexpr int SPC = WARPS * (32 / SX);  // segments per block
   __shared__ double red[32];
   __shared__ ItemCache cache;
   extern __shared__ __align__(16) unsigned char stage_smem[];
@@ -359,58 +434,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_apply_dot_w(const SimDev* 
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
     cache_sim(sims, wi.x, cache, cur, dep);
-    const SimDev& s = cache.s;
-    const Ctl& c = cache.c;
-    if (c.phase != PH_ITER) continue;
-    const Geo g(s);
-    const int tile = wi.y * SPC + (int)threadIdx.x / SX;
-    const bool active = tile < s.w_ntiles;
-    const int tx = tile % s.w_ntx, rem = tile / s.w_ntx, ty = rem % s.w_nty, tz = rem / s.w_nty;
-    const T* __restrict__ r = s.cheb_m >= 2 ? ChebVecs<T>::z(s) : IterVecs<T>::r(s);  // see k_apply_dot
-    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
-    const T* __restrict__ dold = IterVecs<T>::d(s, c.id);
-    T* __restrict__ dnew = IterVecs<T>::d(s, c.id ^ 1);
-    T* __restrict__ q = IterVecs<T>::q(s);
-    const bool rs = c.restart != 0;
-    const T beta = rs ? T(0) : (T)c.beta;
-    T acc = T(0);
-    auto out = [&](int m, bool dir, T y, T v) {
-      const T qv = dir ? T(0) : y;
-      q[m] = qv;
-      dnew[m] = v;
-      acc += v * qv;
-    };
-    if constexpr (STAGES == 0) {
-      warp_tile_op_e<E, T, SX, NY>(
-          g, s, IterVecs<T>::coef(s), active, tx * (SX - 2), ty * NY, tz * s.w_tz, s.w_tz, (T)s.inv_dt,
-          (T)s.theta, true,
-          [&](int m, bool live) -> DirRaw<T> {
-            if (!live) return {T(0), T(0), T(0)};
-            return {pinv[m], r[m], rs ? T(0) : dold[m]};
-          },
-          [&](const DirRaw<T>& v) -> T { return v.p * v.r + beta * v.d; }, out);
-    } else {
-      using CoefT = typename std::remove_cv<typename std::remove_reference<decltype(IterVecs<T>::coef(s)[0])>::type>::type;
-      const LaneGeo<NY> lg(g, active, (int)threadIdx.x % SX, SX, tx * (SX - 2), ty * NY, true, s.sc);
-      AsyncSrc<T, NY, STAGES, CoefT> src(pinv, r, rs ? nullptr : dold, IterVecs<T>::coef(s), beta, stage_smem,
-                                         (int)blockDim.x, (int)threadIdx.x, tz * s.w_tz);
-      warp_march_e<E, T, SX, NY>(lg, s, src, s.w_tz, (T)s.inv_dt, (T)s.theta, out);
-    }
-    const T accv[1] = {acc};
-    double tot[1];
-    if (finish_item<T, 1>(s, wi.y, s.w_items, accv, tot, red)) {
-      SimScalars* sc = s.sc;
-      sc->count = 0;
-      const double dq = tot[0];
-      sc->dq = dq;
-      if (!isfinite(dq)) fail(sc, ST_NONFINITE);
-      else if (!(dq > 0.0)) fail(sc, ST_BREAKDOWN);
-      else {
-        sc->alpha = sc->delta / dq;
-        sc->id ^= 1;
-        sc->restart = 0;
-      }
-    }
+    if (cache.c.phase != PH_ITER) continue;
+    apply_w_item<T, SX, NY, WARPS, STAGES, E, false>(cache.s, cache.c, wi.y, red, stage_smem);
   }
 }
 
@@ -780,8 +805,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_cg_iter(const SimDev* __re
 template <class T> struct Quad;
 template <> struct Quad<float> {
   float v[4];
+  template <bool CG>
   __device__ __forceinline__ void load(const float* p) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
+    const float4 t = ld_vec<CG>(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
   }
   __device__ __forceinline__ void store(float* p) const {
@@ -790,8 +816,10 @@ template <> struct Quad<float> {
 };
 template <> struct Quad<double> {
   double v[4];
+  template <bool CG>
   __device__ __forceinline__ void load(const double* p) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    const double2 a = ld_vec<CG>(reinterpret_cast<const double2*>(p)),
+                  b = ld_vec<CG>(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
   __device__ __forceinline__ void store(double* p) const {
@@ -799,6 +827,122 @@ template <> struct Quad<double> {
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
   }
 };
+
+// One work item of k_update (pw_chunk(QPT) nodes of one simulation in phase
+// PH_ITER). VT > 1: a block of kPwThreads / VT threads does the item, each
+// thread the work of VT threads of a kPwThreads block in the same order, so
+// the item's results and partial are bitwise those of k_update. CG: vectors
+// are loaded through L2 only (see ld_vec). Returns true in thread 0 of the
+// block that finished the simulation's last item when the simulation stays
+// in PH_ITER (another iteration follows).
+template <class T, int P, int QPT, int VT, bool CG>
+__device__ __forceinline__ bool update_item(const SimDev& s, const Ctl& c, int item, double* red) {
+  const bool resid_it = (P == P_FP64) && s.resid_period > 0 && c.iter > 0 && (c.iter % s.resid_period) == 0;
+  const int nn = (int)s.nn;
+  const int base = item * pw_chunk(QPT);
+  const int end = min(base + pw_chunk(QPT), nn);
+  T* __restrict__ x = (P == P_FP64) ? reinterpret_cast<T*>(s.vec64[c.ix]) : reinterpret_cast<T*>(s.e32);
+  T* __restrict__ r = const_cast<T*>(IterVecs<T>::r(s));
+  const T* __restrict__ pinv = IterVecs<T>::pinv(s);
+  const T* __restrict__ d = IterVecs<T>::d(s, c.id);
+  const T* __restrict__ q = IterVecs<T>::q(s);
+  const T alpha = (T)c.alpha;
+  const bool zero_x = (P != P_FP64) && c.iter == 0;  // the inner solve starts from e = 0
+  const int vblock = VT * (int)blockDim.x;             // threads of the block this one stands in for
+  T part[VT];  // per-(virtual-)thread partials in T, FP64 from the warp sums on
+#pragma unroll
+  for (int vt = 0; vt < VT; ++vt) {
+    const int tid = (int)threadIdx.x + vt * (int)blockDim.x;
+    T pacc = T(0);
+    // QPT groups of 4 nodes per thread, group u at base + 4*tid + u*4*vblock
+    // (coalesced per group); every load is issued before any result is used
+    Quad<T> xv[QPT], dv[QPT], rv[QPT], qv[QPT], pv[QPT];
+    bool full[QPT];
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int n = base + 4 * (tid + u * vblock);
+      full[u] = n + 3 < end;
+      if (full[u]) {
+        dv[u].template load<CG>(d + n);
+        if (!zero_x) xv[u].template load<CG>(x + n);
+        if (!resid_it) {
+          rv[u].template load<CG>(r + n);
+          qv[u].template load<CG>(q + n);
+          pv[u].template load<false>(pinv + n);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int n = base + 4 * (tid + u * vblock);
+      if (full[u]) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv[u].v[a] = (zero_x ? T(0) : xv[u].v[a]) + alpha * dv[u].v[a];
+        xv[u].store(x + n);
+        if (!resid_it) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            rv[u].v[a] -= alpha * qv[u].v[a];
+            pacc += rv[u].v[a] * rv[u].v[a] * pv[u].v[a];
+          }
+          rv[u].store(r + n);
+        }
+      } else {
+        for (int m = n; m < end; ++m) {  // ragged end of the mesh
+          x[m] = (zero_x ? T(0) : ld_vec<CG>(x + m)) + alpha * ld_vec<CG>(d + m);
+          if (!resid_it) {
+            const T rn = ld_vec<CG>(r + m) - alpha * ld_vec<CG>(q + m);
+            r[m] = rn;
+            pacc += rn * rn * pinv[m];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < VT; ++k)
+      if (k == vt) part[k] = pacc;
+  }
+  double pd[1];
+  bool more = false;
+  if (finish_item<T, 1, VT>(s, item, s.npw, part, pd, red)) {
+    SimScalars* sc = s.sc;
+    sc->count = 0;
+    if (resid_it) {
+      sc->phase = PH_RESID;  // k_open recomputes r = b - A x and finishes the iteration
+    } else {
+      const double dn = pd[0];
+      // The stopping tests use r^T P^-1 r (Algorithm 1) with either
+      // preconditioner; with Chebyshev passes they form delta = r^T z and beta.
+      const bool ch = s.cheb_m >= 2;
+      if (!ch) {
+        sc->beta = dn / sc->delta;
+        sc->delta = dn;
+      }
+      sc->iter += 1;
+      sc->iter_step += 1;
+      if (!isfinite(dn)) {
+        fail(sc, ST_NONFINITE);
+      } else if (P == P_FP64) {
+        // The recurrence residual drifts from b - A x (by far more than
+        // rounding on stiff systems), so a step closes only on the true
+        // residual: k_open recomputes it and closes or continues.
+        if (dn <= sc->thresh) {
+          sc->confirm = 1;
+          sc->phase = PH_RESID;
+        } else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
+        else if (ch) enter_iter(s, sc);
+        else more = true;
+      } else {
+        const int cap = (s.prec == P_FP32_PLAIN) ? s.max_iter : s.inner_max_iter;
+        if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
+        else if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
+        else if (ch) enter_iter(s, sc);
+        else more = true;
+      }
+    }
+  }
+  return more;
+}
 
 template <class T, int P, int QPT>
 __global__ void __launch_bounds__(kPwThreads, pw_min_blocks(QPT, sizeof(T))) k_update(const SimDev* __restrict__ sims, const int2* __restrict__ work,
@@ -812,101 +956,8 @@ __global__ void __launch_bounds__(kPwThreads, pw_min_blocks(QPT, sizeof(T))) k_u
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
     cache_sim(sims, wi.x, cache, cur, dep);
-    const SimDev& s = cache.s;
-    const Ctl& c = cache.c;
-    if (c.phase != PH_ITER) continue;
-    const bool resid_it = (P == P_FP64) && s.resid_period > 0 && c.iter > 0 && (c.iter % s.resid_period) == 0;
-    const int nn = (int)s.nn;
-    const int base = wi.y * pw_chunk(QPT);
-    const int end = min(base + pw_chunk(QPT), nn);
-    T* __restrict__ x = (P == P_FP64) ? reinterpret_cast<T*>(s.vec64[c.ix]) : reinterpret_cast<T*>(s.e32);
-    T* __restrict__ r = const_cast<T*>(IterVecs<T>::r(s));
-    const T* __restrict__ pinv = IterVecs<T>::pinv(s);
-    const T* __restrict__ d = IterVecs<T>::d(s, c.id);
-    const T* __restrict__ q = IterVecs<T>::q(s);
-    const T alpha = (T)c.alpha;
-    const bool zero_x = (P != P_FP64) && c.iter == 0;  // the inner solve starts from e = 0
-    T part[1] = {T(0)};  // per-thread partial in T, FP64 from the warp sums on
-    // QPT groups of 4 nodes per thread, group u at base + 4*tid + u*4*blockDim
-    // (coalesced per group); every load is issued before any result is used
-    Quad<T> xv[QPT], dv[QPT], rv[QPT], qv[QPT], pv[QPT];
-    bool full[QPT];
-#pragma unroll
-    for (int u = 0; u < QPT; ++u) {
-      const int n = base + 4 * ((int)threadIdx.x + u * (int)blockDim.x);
-      full[u] = n + 3 < end;
-      if (full[u]) {
-        dv[u].load(d + n);
-        if (!zero_x) xv[u].load(x + n);
-        if (!resid_it) {
-          rv[u].load(r + n);
-          qv[u].load(q + n);
-          pv[u].load(pinv + n);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < QPT; ++u) {
-      const int n = base + 4 * ((int)threadIdx.x + u * (int)blockDim.x);
-      if (full[u]) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) xv[u].v[a] = (zero_x ? T(0) : xv[u].v[a]) + alpha * dv[u].v[a];
-        xv[u].store(x + n);
-        if (!resid_it) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            rv[u].v[a] -= alpha * qv[u].v[a];
-            part[0] += rv[u].v[a] * rv[u].v[a] * pv[u].v[a];
-          }
-          rv[u].store(r + n);
-        }
-      } else {
-        for (int m = n; m < end; ++m) {  // ragged end of the mesh
-          x[m] = (zero_x ? T(0) : x[m]) + alpha * d[m];
-          if (!resid_it) {
-            const T rn = r[m] - alpha * q[m];
-            r[m] = rn;
-            part[0] += rn * rn * pinv[m];
-          }
-        }
-      }
-    }
-    double pd[1];
-    if (finish_item<T, 1>(s, wi.y, s.npw, part, pd, red)) {
-      SimScalars* sc = s.sc;
-      sc->count = 0;
-      if (resid_it) {
-        sc->phase = PH_RESID;  // k_open recomputes r = b - A x and finishes the iteration
-      } else {
-        const double dn = pd[0];
-        // The stopping tests use r^T P^-1 r (Algorithm 1) with either
-        // preconditioner; with Chebyshev passes they form delta = r^T z and beta.
-        const bool ch = s.cheb_m >= 2;
-        if (!ch) {
-          sc->beta = dn / sc->delta;
-          sc->delta = dn;
-        }
-        sc->iter += 1;
-        sc->iter_step += 1;
-        if (!isfinite(dn)) {
-          fail(sc, ST_NONFINITE);
-        } else if (P == P_FP64) {
-          // The recurrence residual drifts from b - A x (by far more than
-          // rounding on stiff systems), so a step closes only on the true
-          // residual: k_open recomputes it and closes or continues.
-          if (dn <= sc->thresh) {
-            sc->confirm = 1;
-            sc->phase = PH_RESID;
-          } else if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
-          else if (ch) enter_iter(s, sc);
-        } else {
-          const int cap = (P == P_FP32_PLAIN) ? s.max_iter : s.inner_max_iter;
-          if (sc->iter_step >= s.max_iter) fail(sc, ST_NOT_CONVERGED);
-          else if (dn <= sc->thresh_in || sc->iter >= cap) sc->phase = PH_OUTER;
-          else if (ch) enter_iter(s, sc);
-        }
-      }
-    }
+    if (cache.c.phase != PH_ITER) continue;
+    update_item<T, P, QPT, 1, false>(cache.s, cache.c, wi.y, red);
   }
 }
 

@@ -87,11 +87,11 @@ def test_tuning_table_host_logic(lib):
         api.heat_tuning_variant(n)
     old = api.heat_tuning_get()
     assert old == {"variant": [-1, 0, 0], "seg_nodes": [512, 512, 512], "pw_quads": [2, 4, 4],
-                   "open_w": [2, 2, 2]}
+                   "open_w": [2, 2, 2], "loop": [0, 0, 0]}
     try:
-        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4], [1, 0, 1])
+        api.heat_tuning_set([-1, n - 1, 0], [256, 1024, 2048], [1, 2, 4], [1, 0, 1], [0, 1, 0])
         assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
-                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1]}
+                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1], "loop": [0, 1, 0]}
         no64 = [v for v in range(n) if not shapes[v]["has_fp64"]]
         bad = [([-1, n, 0], [512] * 3), ([-2, 0, 0], [512] * 3), ([-1, 0, 0], [16, 512, 512]),
                ([-1, 0, 0], [512, 512, (1 << 20) + 1])]
@@ -107,11 +107,26 @@ def test_tuning_table_host_logic(lib):
         for ow in ([3, 1, 1], [0, -1, 1]):
             with pytest.raises(api.HeatError):
                 api.heat_tuning_set([-1, 0, 0], [512] * 3, [2, 4, 4], ow)
+        # the persistent iteration is 0 or 1, and only for the FP32 paths
+        for lp in ([1, 0, 0], [0, 2, 0], [0, 0, -1]):
+            with pytest.raises(api.HeatError) as e:
+                api.heat_tuning_set([-1, 0, 0], [512] * 3, [2, 4, 4], [2, 2, 2], lp)
+            assert e.value.status == api.HEAT_ERR_ARG
         # a rejected table leaves the last good one in place
         assert api.heat_tuning_get() == {"variant": [-1, n - 1, 0], "seg_nodes": [256, 1024, 2048],
-                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1]}
+                                         "pw_quads": [1, 2, 4], "open_w": [1, 0, 1], "loop": [0, 1, 0]}
     finally:
-        api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"])
+        api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"], old["loop"])
+
+
+def test_loop_wait_hook_checks_its_arguments(lib):
+    import paper_1905_07622_gb300.api as api
+
+    for extra, limit in ((2, 0.0), (0, -1.0), (1, 61.0), (0, float("nan"))):
+        with pytest.raises(api.HeatError) as e:
+            api.heat_debug_loop_wait(extra, limit)
+        assert e.value.status == api.HEAT_ERR_ARG
+    api.heat_debug_loop_wait(0, 0.0)  # the defaults
 
 
 @pytest.mark.parametrize("bad", ["f32_coef", "short_coef", "short_x", "long_y", "empty_dot", "cpu"])

@@ -22,7 +22,7 @@ def restore_table():
     import paper_1905_07622_gb300 as hg
     old = hg.heat_tuning_get()
     yield
-    hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"])
+    hg.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"], old["loop"])
 
 
 def _problem():

@@ -288,8 +288,9 @@ struct Engine {
   std::vector<int2> h_ow;
   // [0] operator tiles, [1] pointwise chunks, [2] warp-apply items, [3] warp open-pass items
   int* d_nwork = nullptr;
-  int* d_unfinished = nullptr;
-  int* h_unfinished = nullptr;
+  int* d_unfinished = nullptr;  // [2]: the two poll slots of engine_step_all
+  int* h_unfinished = nullptr;  // [2], pinned
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   double* d_partial = nullptr;
   long long cap_op = 0, cap_pw = 0, cap_partial = 0;
   int grid_op = 0, grid_pw = 0, iters_per_tick = 4;
@@ -371,7 +372,7 @@ static heat_status loop_abort(Engine* e) {
     st = sim_write_scalars(s);
     if (st != HEAT_OK) return st;
   }
-  *e->h_abort = 0;
+  e->h_abort[0] = e->h_abort[1] = 0;
   return loop_sync_reset(e);
 }
 
@@ -663,11 +664,13 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
       cudaMalloc(&e->d_work_aw, sizeof(int2) * std::max(1LL, cap_aw)) != cudaSuccess ||
       cudaMalloc(&e->d_work_ow, sizeof(int2) * std::max(1LL, cap_ow)) != cudaSuccess ||
       cudaMalloc(&e->d_nwork, sizeof(int) * 4) != cudaSuccess ||
-      cudaMalloc(&e->d_unfinished, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_unfinished, 2 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_partial, sizeof(double) * 4 * cap_partial) != cudaSuccess ||
-      cudaMallocHost(&e->h_unfinished, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&e->h_unfinished, 2 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_sync, sizeof(GridSync)) != cudaSuccess ||
-      cudaMallocHost(&e->h_abort, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&e->h_abort, 2 * sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->poll_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->poll_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_error(HEAT_ERR_NOMEM, "engine: device allocation failed"));
   }
@@ -681,7 +684,7 @@ heat_status engine_create(heat_sim* const* sims, int nsims, int precision, cudaS
   }
   st = engine_upload(e);
   if (st != HEAT_OK) return fail(st);
-  *e->h_abort = 0;
+  e->h_abort[0] = e->h_abort[1] = 0;
   st = loop_sync_reset(e);
   if (st != HEAT_OK) return fail(st);
   st = engine_capture(e);
@@ -706,6 +709,8 @@ void engine_destroy(Engine* e) {
   if (e->d_sync) cudaFree(e->d_sync);
   if (e->h_abort) cudaFreeHost(e->h_abort);
   if (e->h_unfinished) cudaFreeHost(e->h_unfinished);
+  for (cudaEvent_t ev : e->poll_ev)
+    if (ev) cudaEventDestroy(ev);
   if (e->d_phases) cudaFree(e->d_phases);
   if (e->h_phases) cudaFreeHost(e->h_phases);
   delete e;
@@ -805,23 +810,41 @@ heat_status engine_step_all(Engine* e, int nsteps, heat_step_stats* stats, int r
   const long long max_ticks = (long long)nsteps * (max_iter + 2LL * max_outer + 4) + 64;
   long long ticks = 0;
   e->launches = 0;
-  for (;;) {
+  // Batch b of ticks_per_poll ticks ends with a count of the unfinished
+  // members (and the persistent loop's abort flag) copied to slot b & 1 and
+  // an event. The first batch is waited for at once (a short call leaves no
+  // idle ticks behind); from then on batch b is queued before the host waits
+  // for batch b - 1, so the GPU does not idle while the host polls. At most
+  // one batch of idle ticks runs after the last member finishes.
+  for (long long b = 0;; ++b) {
+    const int slot = (int)(b & 1);
     for (int t = 0; t < ticks_per_poll; ++t) CUDA_TRY(cudaGraphLaunch(e->gexec, e->stream));
     ticks += ticks_per_poll;
     e->launches += (long long)ticks_per_poll * tick_launches(e) + 1;
-    k_count_unfinished<<<1, 256, 0, e->stream>>>(e->d_sims, (int)e->sims.size(), e->d_unfinished);
+    k_count_unfinished<<<1, 256, 0, e->stream>>>(e->d_sims, (int)e->sims.size(), e->d_unfinished + slot);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemcpyAsync(e->h_unfinished, e->d_unfinished, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CUDA_TRY(cudaMemcpyAsync(e->h_unfinished + slot, e->d_unfinished + slot, sizeof(int), cudaMemcpyDeviceToHost,
+                             e->stream));
     if (e->ks.loop)
-      CUDA_TRY(cudaMemcpyAsync(e->h_abort, &e->d_sync->abort, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
-    CUDA_TRY(cudaStreamSynchronize(e->stream));
-    if (e->ks.loop && *e->h_abort) {
+      CUDA_TRY(cudaMemcpyAsync(e->h_abort + slot, &e->d_sync->abort, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CUDA_TRY(cudaEventRecord(e->poll_ev[slot], e->stream));
+    long long waited = -1;  // the batch whose counts are read now
+    if (b == 0) waited = 0;
+    else if (b >= 2) waited = b - 1;
+    if (waited < 0) continue;  // batch 1 queued right after batch 0 was read
+    const int ws = (int)(waited & 1);
+    CUDA_TRY(cudaEventSynchronize(e->poll_ev[ws]));
+    if (e->ks.loop && e->h_abort[ws]) {
+      CUDA_TRY(cudaStreamSynchronize(e->stream));
       heat_status st = loop_abort(e);
       if (st != HEAT_OK) return st;
       break;
     }
-    if (*e->h_unfinished == 0) break;
-    if (ticks > max_ticks) return set_error(HEAT_ERR_TIMEOUT, "engine: solve did not finish within %lld ticks", ticks);
+    if (e->h_unfinished[ws] == 0) break;
+    if (ticks > max_ticks) {
+      cudaStreamSynchronize(e->stream);
+      return set_error(HEAT_ERR_TIMEOUT, "engine: solve did not finish within %lld ticks", ticks);
+    }
   }
   heat_status first_bad = HEAT_OK;
   for (size_t i = 0; i < e->sims.size(); ++i) {

@@ -293,7 +293,7 @@ struct Engine {
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   double* d_partial = nullptr;
   long long cap_op = 0, cap_pw = 0, cap_partial = 0;
-  int grid_op = 0, grid_pw = 0, iters_per_tick = 4;
+  int grid_op = 0, grid_pw = 0, iters_per_tick = 6;
   int elem = E_Q1;  // the members' finite element (one per engine)
   int ncheb = 0;    // Chebyshev passes per iteration in the tick: max over members of degree - 1
   int grid_ch = 0;  // grid of the pass kernel

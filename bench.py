@@ -489,6 +489,7 @@ def run_persistent(hg, torch, stream, headline_table, batch_table, nsteps_single
     iteration), each under its own table, on the first steps of the headline
     workload and of the batched one. Same work items, so with equal item sizes
     the fields are bitwise equal (checked here on the headline)."""
+    import numpy as np
     import workloads as W
     base = hg.heat_tuning_get()
     pid = hg.PRECISIONS["fp32_refined"]

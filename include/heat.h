@@ -585,7 +585,10 @@ heat_status heat_tuning_set(const heat_tuning* t);
  * tick graph of its engine, about `reps` iterations after 8 warm-up ones,
  * every iteration on a seeded residual that does not converge) for every
  * candidate (block tile; each variant with a segment size of 256, 512, 1024
- * or 2048 nodes) on this simulation's mesh and precision, and store the
+ * or 2048 nodes; then, for the fastest variant, the segment sizes whose work
+ * items fill whole waves of resident blocks best; then the pointwise item
+ * sizes and the persistent iteration) on this simulation's mesh and
+ * precision, and store the
  * fastest in the table entries of that precision and of the mesh's size
  * bucket. Outputs the resulting table and the winner's mean ms per iteration
  * (either may be NULL). Needs a prior heat_step; leaves the simulation's solver state

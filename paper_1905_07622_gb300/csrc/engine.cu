@@ -1174,6 +1174,50 @@ heat_status engine_time_iterations(Engine* e, int reps, double* ms_per_iter) {
   return HEAT_OK;
 }
 
+// Segment sizes (output nodes per warp-segment tile) for table t's warp
+// apply of precision prec on these simulations whose work items fill whole
+// waves of resident blocks: for each count of waves, the largest levels per
+// tile that keep the items within it, kept when the waves are at least 85%
+// full; at most four, fewest waves first. Empty for the block-tile apply.
+static std::vector<int> wave_segments(heat_sim* const* sims, int nsims, int prec, const Tuning& t, int bucket) {
+  std::vector<int> out;
+  const KernelSet ks = kernel_set(prec, t, members_ncheb_of(sims, nsims) > 0, sims[0]->dev.elem);
+  if (!ks.apply_w) return out;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.apply_w, 32 * ks.wwarps, ks.apply_w_smem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    return out;
+  }
+  const long long cap = (long long)sm_count() * occ;
+  const int per_level = (ks.wsx - 2) * ks.wny;
+  const int levels = sims[0]->dev.nz + 1;
+  long long best_items_for_waves[5] = {0, 0, 0, 0, 0};
+  int best_seg_for_waves[5] = {0, 0, 0, 0, 0};
+  for (int tz0 = levels; tz0 >= 4; --tz0) {
+    const int seg = tz0 * per_level;
+    if (seg > (1 << 20)) continue;
+    KernelSet k2 = ks;
+    k2.seg_nodes[bucket] = seg;
+    long long items = 0;
+    for (int i = 0; i < nsims; ++i) {
+      SimDev d = sims[i]->dev;
+      tile_geometry(d, k2);
+      items += d.w_items;
+    }
+    const long long waves = (items + cap - 1) / cap;
+    if (waves < 1 || waves > 4) continue;
+    if (items > best_items_for_waves[waves]) {  // the fullest last wave, largest tiles on ties
+      best_items_for_waves[waves] = items;
+      best_seg_for_waves[waves] = seg;
+    }
+  }
+  for (int w = 1; w <= 4; ++w)
+    if (best_seg_for_waves[w] && best_items_for_waves[w] >= (long long)(0.85 * (double)(w * cap)))
+      out.push_back(best_seg_for_waves[w]);
+  return out;
+}
+
 heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* best_variant, int* best_seg,
                             double* best_ms) {
   static const int kSegs[] = {256, 512, 1024, 2048};
@@ -1201,6 +1245,30 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
         best_t = ms;
         best = t;
       }
+    }
+  }
+  // then wave-aligned segment sizes for the chosen warp apply: the levels
+  // per segment tile whose total work items fill the resident blocks
+  // (SMs x blocks per SM) best, a few waves at most (a launch whose last
+  // wave is partly empty leaves SMs idle: on the 100^3 mesh 338 items on
+  // 456 resident blocks run three blocks on some SMs and two on the others)
+  for (int seg : wave_segments(sims, nsims, prec, best, bucket)) {
+    if (st != HEAT_OK) break;
+    bool tried = false;
+    for (int k : kSegs) tried = tried || k == seg;
+    if (tried) continue;
+    Tuning t = best;
+    t.seg_nodes[bucket] = seg;
+    Engine* e = nullptr;
+    st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
+    if (st != HEAT_OK) break;
+    double ms = 0.0;
+    st = engine_time_iterations(e, 8, &ms);
+    if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
+    engine_destroy(e);
+    if (st == HEAT_OK && ms < best_t) {
+      best_t = ms;
+      best = t;
     }
   }
   // then the pointwise kernel's item size with the chosen apply

@@ -139,7 +139,11 @@ def test_autotune_picks_a_valid_entry_and_keeps_parity(precision):
         assert v == -1 or (0 <= v < hg.heat_tuning_num_variants())
         if v >= 0 and precision == "fp64":
             assert hg.heat_tuning_variant(v)["has_fp64"]
-        assert table["seg_nodes"][0] in (256, 512, 1024, 2048)
+        seg = table["seg_nodes"][0]
+        if seg not in (256, 512, 1024, 2048):  # a wave-aligned size: whole levels of the chosen segment tile
+            assert v >= 0, seg
+            shape = hg.heat_tuning_variant(v)
+            assert seg % ((shape["seg_width"] - 2) * shape["rows"]) == 0, (v, seg)
         # entries of the other precisions and size buckets are untouched
         for q in range(3):
             if q != pid:

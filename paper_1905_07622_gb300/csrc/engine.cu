@@ -40,6 +40,7 @@ struct KernelSet {
   // `open` when set), on their own segment geometry and work list
   TileFn open_w = nullptr;
   int owsx = 0, owny = 0, owwarps = 0;
+  long long open_cap = 0;  // blocks of open_w resident on the GPU at once (0: unknown)
   // the CG iterations of a tick as one persistent kernel (replaces the
   // apply and update launches when set; FP32 paths, register-prefetch apply)
   LoopFn loop = nullptr;
@@ -197,6 +198,8 @@ static TileFn update_kernel(int prec, int qpt) {
   }
 }
 
+static int sm_count();
+
 // The kernels of precision prec under tuning table t. With Chebyshev passes
 // (cheb) a fused variant is replaced by the register-prefetch variant of the
 // same segment shape: the fused iteration has no place for the passes.
@@ -244,6 +247,11 @@ static KernelSet kernel_set(int prec, const Tuning& t, bool cheb = false, int el
     k.owsx = kOpenSX;
     k.owny = open_w_rows(t.open_w[prec]);
     k.owwarps = kOpenWarps;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.open_w, 32 * kOpenWarps, 0) == cudaSuccess && occ > 0)
+      k.open_cap = (long long)sm_count() * occ;
+    else
+      cudaGetLastError();
   }
   for (int b = 0; b < 3; ++b) k.seg_nodes[b] = t.seg_nodes[b];
   const int qpt = t.pw_quads[prec];
@@ -422,11 +430,31 @@ static void tile_geometry(SimDev& d, const KernelSet& ks) {
     constexpr int kOpenSegNodes = 1024;
     d.o_ntx = (d.nx + 1 + ks.owsx - 3) / (ks.owsx - 2);
     d.o_nty = (d.ny + 1 + ks.owny - 1) / ks.owny;
-    const int tz0 = std::max(4, std::min(levels, kOpenSegNodes / ((ks.owsx - 2) * ks.owny)));
+    const long long cols = (long long)d.o_ntx * d.o_nty;
+    const int spc = ks.owwarps * (32 / ks.owsx);
+    const int tz_def = std::max(4, std::min(levels, kOpenSegNodes / ((ks.owsx - 2) * ks.owny)));
+    auto items_for = [&](int tz) { return (cols * ((levels + tz - 1) / tz) + spc - 1) / spc; };
+    int tz0 = tz_def;
+    // A mesh whose passes fill at least half of the resident blocks in at
+    // most two waves takes the tile height in [tz_def / 2, tz_def] whose
+    // items fill the waves best (the 100^3 mesh: 404 items of 26 levels on
+    // 456 resident blocks instead of 303 of 34). It depends on the mesh and
+    // the GPU only, so a simulation's passes stay the same alone and in a batch.
+    const long long cap = ks.open_cap, items_def = items_for(tz_def);
+    if (cap > 0 && 2 * items_def >= cap && items_def <= 2 * cap) {
+      double best = -1.0;
+      for (int tz = tz_def; tz >= std::max(4, tz_def / 2); --tz) {
+        const long long it = items_for(tz), waves = (it + cap - 1) / cap;
+        const double eff = (double)it / (double)(waves * cap);
+        if (eff > best + 1e-12) {
+          best = eff;
+          tz0 = tz;
+        }
+      }
+    }
     d.o_ntz = (levels + tz0 - 1) / tz0;
     d.o_tz = (levels + d.o_ntz - 1) / d.o_ntz;
     d.o_ntiles = d.o_ntx * d.o_nty * d.o_ntz;
-    const int spc = ks.owwarps * (32 / ks.owsx);
     d.o_items = (d.o_ntiles + spc - 1) / spc;
   }
 }

@@ -585,7 +585,7 @@ heat_status heat_tuning_set(const heat_tuning* t);
  * tick graph of its engine, about `reps` iterations after 8 warm-up ones,
  * every iteration on a seeded residual that does not converge) for every
  * candidate (block tile; each variant with a segment size of 256, 512, 1024
- * or 2048 nodes; then, for the fastest variant, the segment sizes whose work
+ * or 2048 nodes; then, for the two fastest variants, the segment sizes whose work
  * items fill whole waves of resident blocks best; then the pointwise item
  * sizes and the persistent iteration) on this simulation's mesh and
  * precision, and store the

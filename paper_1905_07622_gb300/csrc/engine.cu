@@ -1255,6 +1255,8 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
   Tuning best = base;
   double best_t = 1e300;
   heat_status st = HEAT_OK;
+  // each warp variant's best time over the fixed segment sizes
+  std::vector<double> vbest(kNumVariants, 1e300);
   for (int v = -1; v < kNumVariants && st == HEAT_OK; ++v) {
     if (v >= 0 && prec == P_FP64 && !kVariants[v].f64[0]) continue;
     for (int si = 0; si < (v < 0 ? 1 : 4) && st == HEAT_OK; ++si) {
@@ -1269,34 +1271,50 @@ heat_status engine_autotune(heat_sim* const* sims, int nsims, int reps, int* bes
       st = engine_time_iterations(e, 8, &ms);  // warm-up
       if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
       engine_destroy(e);
+      if (st == HEAT_OK && v >= 0) vbest[v] = std::min(vbest[v], ms);
       if (st == HEAT_OK && ms < best_t) {
         best_t = ms;
         best = t;
       }
     }
   }
-  // then wave-aligned segment sizes for the chosen warp apply: the levels
+  // then wave-aligned segment sizes for the two fastest warp applies: the levels
   // per segment tile whose total work items fill the resident blocks
   // (SMs x blocks per SM) best, a few waves at most (a launch whose last
   // wave is partly empty leaves SMs idle: on the 100^3 mesh 338 items on
   // 456 resident blocks run three blocks on some SMs and two on the others)
-  for (int seg : wave_segments(sims, nsims, prec, best, bucket)) {
-    if (st != HEAT_OK) break;
-    bool tried = false;
-    for (int k : kSegs) tried = tried || k == seg;
-    if (tried) continue;
-    Tuning t = best;
-    t.seg_nodes[bucket] = seg;
-    Engine* e = nullptr;
-    st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
-    if (st != HEAT_OK) break;
-    double ms = 0.0;
-    st = engine_time_iterations(e, 8, &ms);
-    if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
-    engine_destroy(e);
-    if (st == HEAT_OK && ms < best_t) {
-      best_t = ms;
-      best = t;
+  int top[2] = {-1, -1};
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (vbest[v] >= 1e300) continue;
+    if (top[0] < 0 || vbest[v] < vbest[top[0]]) {
+      top[1] = top[0];
+      top[0] = v;
+    } else if (top[1] < 0 || vbest[v] < vbest[top[1]]) {
+      top[1] = v;
+    }
+  }
+  for (int v : top) {
+    if (v < 0 || st != HEAT_OK) continue;
+    Tuning tv = base;
+    tv.variant[prec] = v;
+    for (int seg : wave_segments(sims, nsims, prec, tv, bucket)) {
+      if (st != HEAT_OK) break;
+      bool tried = false;
+      for (int k : kSegs) tried = tried || k == seg;
+      if (tried) continue;
+      Tuning t = tv;
+      t.seg_nodes[bucket] = seg;
+      Engine* e = nullptr;
+      st = engine_create(sims, nsims, prec, sims[0]->stream, &e, &t);
+      if (st != HEAT_OK) break;
+      double ms = 0.0;
+      st = engine_time_iterations(e, 8, &ms);
+      if (st == HEAT_OK) st = engine_time_iterations(e, reps, &ms);
+      engine_destroy(e);
+      if (st == HEAT_OK && ms < best_t) {
+        best_t = ms;
+        best = t;
+      }
     }
   }
   // then the pointwise kernel's item size with the chosen apply

@@ -103,8 +103,10 @@ static void finish_request(heat_server* srv, Req* q, heat_status status) {
   srv->cv_done.notify_all();
 }
 
-// Ticks launched between two reads of the members' phases (and admissions).
-constexpr int kTicksPerPoll = 8;
+// Ticks launched between two reads of the members' phases (and admissions):
+// about 30 CG iterations at six per tick. Longer rounds keep a finished
+// request's slot idle for longer before the next admission takes it.
+constexpr int kTicksPerPoll = 5;
 // Work-list and descriptor capacity of a server engine relative to the member
 // set it is built for: later sets that fit run under the same captured graph.
 constexpr double kEngineHeadroom = 2.0;

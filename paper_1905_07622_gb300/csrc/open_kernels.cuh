@@ -29,7 +29,7 @@ template <int P> using OpenT = typename std::conditional<P == P_FP64, double, DF
 // tile_op. opA(mask, fetch, value, out) is the same with (sa, sb) = (1/dt,
 // theta), the A operator, which may read the per-element coefficients
 // precomputed for it. part receives r.P^-1 r (FP64), b.P^-1 b and
-// r32.P^-1 r32.
+// r32.P^-1 r32 (each thread's terms summed in FP32 first).
 // ---------------------------------------------- the A operator, precomputed
 
 // The A operator's Walsh-pair coefficients of one element (SimDev::acoef):
@@ -249,6 +249,9 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
     return dirichlet_value(s, rem - jj * g.px, jj, kk);
   };
   auto ident = [](double v) { return v; };
+  // r32^T P^-1 r32, the restarted inner solve's delta: summed per thread in
+  // FP32 like the inner iterations' norms, FP64 from the block sum on
+  float acc2 = 0.f;
   if (phase == PH_OPEN) {
     const double* __restrict__ u1 = s.vec64[c.iu1];
     const double* __restrict__ u2 = s.vec64[c.iu2];
@@ -285,7 +288,7 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
               const double rn = bn - (hp ? 2.0 * y1[m] - y2[m] : y1[m]);
               const float r32 = (float)rn;
               r32out[m] = r32;
-              part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+              acc2 += r32 * r32 * s.pinv32[m];
               part[0] += rn * rn * pinv[m];
             }
           }
@@ -311,7 +314,7 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
           } else {
             const float r32 = (float)rn;
             r32out[m] = r32;
-            part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+            acc2 += r32 * r32 * s.pinv32[m];
           }
           part[0] += rn * rn * pinv[m];
         });
@@ -339,7 +342,7 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
           }
           const float r32 = (float)rn;
           r32out[m] = r32;
-          part[2] += (double)r32 * (double)r32 * (double)s.pinv32[m];
+          acc2 += r32 * r32 * s.pinv32[m];
           part[0] += rn * rn * pinv[m];
         });
   } else {  // PH_RESID (FP64): r = b - A' x, x already advanced by k_update
@@ -354,6 +357,7 @@ __device__ __forceinline__ void open_passes(const SimDev& s, const Ctl& c, const
           part[0] += rn * rn * pinv[m];
         });
   }
+  part[2] += (double)acc2;
 }
 
 // The last block's update of a simulation's scalars after its open passes

@@ -119,6 +119,15 @@ def test_tuning_table_host_logic(lib):
         api.heat_tuning_set(old["variant"], old["seg_nodes"], old["pw_quads"], old["open_w"], old["loop"])
 
 
+def test_grid_barrier_probe_checks_its_arguments(lib):
+    import paper_1905_07622_gb300.api as api
+
+    for bps, reps in ((0, 10), (17, 10), (1, 0), (1, 100001)):
+        with pytest.raises(api.HeatError) as e:
+            api.heat_probe_grid_barrier(bps, reps)
+        assert e.value.status == api.HEAT_ERR_ARG
+
+
 def test_loop_wait_hook_checks_its_arguments(lib):
     import paper_1905_07622_gb300.api as api
 

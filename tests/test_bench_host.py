@@ -33,3 +33,21 @@ def test_cheb_degree_list_parsing():
     assert bench.cheb_degrees(A) == (2, 3)
     A.cheb_degrees = ""
     assert bench.cheb_degrees(A) == ()
+
+
+def test_tuning_tables_pass_every_entry_through():
+    """A tuned table (as heat_tuning_get returns it) is set again with all
+    five entries; entries a table lacks are left to the library (None)."""
+    calls = []
+
+    class FakeLib:
+        @staticmethod
+        def heat_tuning_set(*args):
+            calls.append(args)
+
+    t = {"variant": [-1, 1, 0], "seg_nodes": [512, 720, 512], "pw_quads": [2, 4, 4], "open_w": [2, 2, 2],
+         "loop": [0, 1, 0]}
+    bench.set_table(FakeLib, t)
+    assert calls[-1] == (t["variant"], t["seg_nodes"], t["pw_quads"], t["open_w"], t["loop"])
+    bench.set_table(FakeLib, {"variant": [-1, 0, 0], "seg_nodes": [512] * 3})
+    assert calls[-1] == ([-1, 0, 0], [512] * 3, None, None, None)
